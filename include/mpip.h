@@ -1,0 +1,196 @@
+/*
+ * mpip.h - C ABI of the GB300 (sm_103a) library for energy-and-force
+ * evaluation of a depth-pruned message-passing interatomic potential on a
+ * periodic system split into spatial partitions with ghost halos.
+ *
+ * Paper: "Scalable Foundation Interatomic Potentials via Message-Passing
+ * Pruning and Graph Partitioning" (arXiv 2509.21694).
+ *   - depth pruning: keep the first K of the backbone's message-passing
+ *     layers and read the energy from layer K (Methods, "Message Passing
+ *     Depth Pruning");
+ *   - partitioning: spatial-grid root sets (Stage 1) extended by a K-hop
+ *     neighbourhood (Stage 2), processed one after another on one GPU
+ *     (Methods, "Graph Partitioning"; Results, Table 2 single-GPU columns);
+ *   - output integration: E is the sum of root energies, F the sum over
+ *     partitions of the gradients of root energies (Methods, "Global Output
+ *     Integration").
+ * The paper leaves the network equations open; the network computed here
+ * is fixed in the oracle's model module header and in the design notes.
+ *
+ * Conventions (all calls):
+ *   - Units: Angstrom, eV, amu, fs.
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; h_* and
+ *     plain pointers are HOST pointers.  The library never frees caller
+ *     memory.  Opaque objects (mp_ctx, mp_graph, mp_plan) are owned by the
+ *     library and released with their *_free / mp_destroy call.
+ *   - Every call enqueues work on the context's CUDA stream and returns
+ *     without synchronising, except where a call documents a host read-back.
+ *   - Return value: MP_OK (0) or a negative MP_ERR_* code; nothing is thrown
+ *     across the ABI and no kernel traps.  mp_strerror() names a code.
+ *   - Atom arrays are in the caller's atom order.  Internally atoms are
+ *     re-ordered by spatial cell; the re-ordering is invisible at the ABI.
+ *   - Box: orthorhombic, periodic in x, y and z, every edge >= 2 r_c.
+ */
+#ifndef MPIP_H
+#define MPIP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MP_OK                  0
+#define MP_ERR_ARG            -1  /* bad argument (null, size, mode)           */
+#define MP_ERR_BOX_TOO_SMALL  -2  /* some box edge < 2 r_c                      */
+#define MP_ERR_OVERLAP        -3  /* two atoms closer than 1e-3 Angstrom        */
+#define MP_ERR_CAPACITY       -4  /* internal buffer too small (retried inside) */
+#define MP_ERR_CUDA           -5  /* a CUDA runtime call failed                 */
+#define MP_ERR_NOT_FINITE     -6  /* NaN or Inf in energy or forces             */
+#define MP_ERR_NOMEM          -7  /* device allocation failed                   */
+#define MP_ERR_UNSUPPORTED    -8  /* model shape not compiled in (F, lmax, ...) */
+#define MP_ERR_TIMEOUT        -9  /* a bounded wait ran out                     */
+
+/* ---- precision and partition modes --------------------------------------- */
+#define MP_FP32  0   /* every contraction in FP32 on CUDA cores               */
+#define MP_BF16  1   /* radial-MLP and node GEMM operands in BF16 on tcgen05
+                        tensor cores, FP32 accumulation; geometry, messages,
+                        features and forces stay FP32                         */
+#define MP_HALO_GEOM 0   /* halo = atoms within K r_c (z) of the slab         */
+#define MP_HALO_BFS  1   /* halo = atoms within K edges of a root (Stage 2)   */
+
+typedef struct mp_ctx   mp_ctx;
+typedef struct mp_graph mp_graph;
+typedef struct mp_plan  mp_plan;
+
+/* Model hyper-parameters.  Compiled shapes: F in {64, 128}, lmax in {1, 2},
+ * H = 64, n_basis = 8, head_hidden = 32. */
+typedef struct {
+    int32_t n_species;      /* S, species indices are 0..S-1                */
+    int32_t F;              /* channels per (l, m) block                    */
+    int32_t lmax;           /* highest spherical-harmonic degree            */
+    int32_t n_layers_full;  /* L_full: layers with weights                  */
+    int32_t H;              /* radial MLP hidden width                      */
+    int32_t n_basis;        /* Bessel functions                             */
+    int32_t p_env;          /* envelope exponent p                          */
+    int32_t head_hidden;    /* correction-head hidden width                 */
+    double  r_cut;          /* cutoff radius r_c                            */
+    double  n_avg;          /* message normaliser (constant)                */
+    double  rep_eps;        /* pair repulsion strength (0 = off)            */
+    double  rep_sigma;      /* pair repulsion length                        */
+} mp_model_desc;
+
+/* Number of doubles in the packed weight vector for desc (see mp_create). */
+int mp_weights_count(const mp_model_desc* desc, int64_t* n_out);
+
+/* Create a context bound to cuda_stream (a cudaStream_t; NULL = legacy
+ * default stream) on the current device.  weights: host array of
+ * mp_weights_count() doubles, copied (converted to FP32 and BF16 device
+ * copies) before return.  Packing order, every tensor row-major, "out = W in":
+ *   emb[S][F], e0[S], w_out[F],
+ *   head_W1[Hh][F], head_b1[Hh], head_W2[Hh], head_b2[1],
+ *   then per layer t = 0..L_full-1:
+ *     W1[H][n_basis], W2[H][H], W3[P][H] (P = F(1+2 lmax), rows ordered
+ *     R0, R1a, R1b, R2a, R2b, F rows each), W0[F][F], U1[F][F], U2[F][F]
+ *     (lmax = 2 only), b[F], V1[F][F], V2[F][F] (lmax = 2 only).
+ * Errors: MP_ERR_ARG, MP_ERR_UNSUPPORTED, MP_ERR_NOMEM, MP_ERR_CUDA. */
+int mp_create(mp_ctx** ctx_out, const mp_model_desc* desc, const double* weights,
+              int64_t n_weights, void* cuda_stream);
+int mp_set_stream(mp_ctx* ctx, void* cuda_stream);
+void mp_destroy(mp_ctx* ctx);
+
+/* Replace the correction-head parameters (head_W1, head_b1, head_W2,
+ * head_b2 packed as in mp_create) from a HOST array. */
+int mp_set_head(mp_ctx* ctx, const double* head_params, int64_t n);
+
+/* ---- neighbour list (periodic cell list) ---------------------------------
+ * Builds the directed edge set of the atom graph: (i <- j, image shift n)
+ * with i != j and |r_j - r_i + n L| < r_c, decided in FP64 with the
+ * canonical wrap x_w = x - L floor(x / L) and the minimum image
+ * n = -rint((x_w[j] - x_w[i]) / L) per axis (the graph the paper's message
+ * passing and its K-hop neighbourhoods run on, Methods "Graph
+ * Partitioning").  The result is bit-exact with an FP64 O(N^2) search.
+ *   d_pos  [n][3] double, caller's order, any (unwrapped) coordinates.
+ *   box    host double[3], edge lengths.
+ * The graph keeps its own wrapped copy of the positions, the cell order and
+ * a receiver-sorted CSR.  Errors: MP_ERR_ARG, MP_ERR_BOX_TOO_SMALL,
+ * MP_ERR_NOMEM, MP_ERR_CUDA. */
+int mp_build_neighbors(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3],
+                       mp_graph** graph_out);
+/* Host read-back (synchronises): atom and directed-edge counts. */
+int mp_graph_info(const mp_graph* g, int64_t* n_atoms, int64_t* n_edges);
+/* Edge list in the CALLER's atom ids: d_recv, d_send int32 [n_edges],
+ * d_shift int8 [n_edges] with code (n_x+1)*9 + (n_y+1)*3 + (n_z+1).  Order:
+ * grouped by receiver in cell order, senders ascending in cell order. */
+int mp_graph_export(const mp_graph* g, int32_t* d_recv, int32_t* d_send, int8_t* d_shift);
+void mp_graph_free(mp_graph* g);
+
+/* ---- partition (Stage 1 + Stage 2) ----------------------------------------
+ * Root sets: P uniform bins of the scaled z coordinate, bin =
+ * min(floor(x_w,z / L_z * P), P - 1) (Stage 1, spatial grid).  Halo:
+ * MP_HALO_BFS = atoms within k_hops edges of a root (Stage 2);
+ * MP_HALO_GEOM = atoms whose periodic z-distance to the slab
+ * [L_z p / P, L_z (p+1) / P) is below k_hops r_c + 1e-6 (a superset).  Each
+ * partition keeps the edges with both ends in its extended set.
+ *   halo_factor_out  host, may be NULL: H = sum_p #halo_p / N (Supplementary
+ *                    S1's halo growth factor).
+ * Errors: MP_ERR_ARG, MP_ERR_NOMEM, MP_ERR_CUDA. */
+int mp_partition(mp_ctx* ctx, const mp_graph* g, int n_parts, int k_hops, int mode,
+                 mp_plan** plan_out, double* halo_factor_out);
+/* Host read-back: sizes of partition p. */
+int mp_plan_info(const mp_plan* plan, int p, int64_t* n_ext, int64_t* n_root, int64_t* n_edges);
+/* Extended set of partition p in caller ids (ascending cell order) and a
+ * root flag per entry: d_gid int32 [n_ext], d_is_root uint8 [n_ext]. */
+int mp_plan_export(const mp_plan* plan, int p, int32_t* d_gid, uint8_t* d_is_root);
+void mp_plan_free(mp_plan* plan);
+
+/* ---- energy and forces ----------------------------------------------------
+ * Evaluates the first n_layers layers (the pruned model when n_layers <
+ * L_full) and F = -dE/dr by a hand-written adjoint, either on the whole
+ * graph (plan == NULL) or partition by partition with the adjoint seeded on
+ * roots only and the results summed (Methods, "Global Output Integration").
+ *   d_pos      [n][3] double, the positions g was built from.
+ *   d_species  [n] int32 in 0..S-1.
+ *   precision  MP_FP32 or MP_BF16.   use_head: add the correction head.
+ *   d_energy   [1] double, written (FP64 sum of per-atom energies).
+ *   d_forces   [n][3] float, written.
+ *   d_e_atom   [n] double per-atom energies, or NULL.
+ * Errors: MP_ERR_ARG, MP_ERR_UNSUPPORTED, MP_ERR_NOMEM, MP_ERR_CUDA. */
+int mp_energy_forces(mp_ctx* ctx, const double* d_pos, const int32_t* d_species,
+                     const mp_graph* g, const mp_plan* plan, int n_layers, int precision,
+                     int use_head, double* d_energy, float* d_forces, double* d_e_atom);
+
+/* ---- molecular dynamics ------------------------------------------------ */
+typedef struct {
+    int32_t n_layers;       /* K                                             */
+    int32_t precision;      /* MP_FP32 / MP_BF16                             */
+    int32_t n_parts;        /* partitions (1 = unpartitioned)                */
+    int32_t k_hops;         /* halo depth in hops / in units of r_c          */
+    int32_t halo_mode;      /* MP_HALO_GEOM / MP_HALO_BFS                    */
+    int32_t use_head;       /* add the correction head                       */
+    int32_t forces_valid;   /* d_forces already holds F(d_pos)               */
+    int32_t check_every;    /* read the error word every n steps (0 = end)   */
+} mp_md_opts;
+
+/* n_steps velocity-Verlet NVE steps (v += dt/2 a; r += dt v, wrapped; new
+ * neighbours, partitions and forces; v += dt/2 a) with a = kappa F / m,
+ * kappa = 9.648533212e-3 Angstrom/fs^2 per eV/(Angstrom amu).
+ *   d_pos, d_vel  [n][3] double, updated in place (positions stay wrapped).
+ *   d_forces      [n][3] float: forces at the final positions on return.
+ *   d_mass        [n] double amu.   dt_fs: time step.
+ *   h_ledger      host double [n_steps][3] = (PE, KE, PE + KE) after each
+ *                 step, or NULL.  Copied back at the end (synchronises).
+ * Errors: as mp_build_neighbors / mp_energy_forces, MP_ERR_NOT_FINITE. */
+int mp_md_step(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces,
+               const double* d_mass, const int32_t* d_species, int64_t n,
+               const double box[3], double dt_fs, int n_steps, const mp_md_opts* opts,
+               double* h_ledger);
+
+const char* mp_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPIP_H */

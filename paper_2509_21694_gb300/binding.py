@@ -1,0 +1,305 @@
+"""Thin ctypes binding of the C ABI declared in include/mpip.h.
+
+Functions keep the C names (mp_create, mp_build_neighbors, mp_partition,
+mp_energy_forces, mp_md_step, ...) and only marshal arguments: torch CUDA
+tensors are passed as raw device pointers, the context runs on the caller's
+current torch CUDA stream.  Every step of the computation runs in the
+library's CUDA kernels; if libmpip.so is missing this module raises at
+import time instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpip.so")
+
+MP_OK = 0
+MP_FP32, MP_BF16 = 0, 1
+MP_HALO_GEOM, MP_HALO_BFS = 0, 1
+ERRORS = {-1: "MP_ERR_ARG", -2: "MP_ERR_BOX_TOO_SMALL", -3: "MP_ERR_OVERLAP",
+          -4: "MP_ERR_CAPACITY", -5: "MP_ERR_CUDA", -6: "MP_ERR_NOT_FINITE",
+          -7: "MP_ERR_NOMEM", -8: "MP_ERR_UNSUPPORTED", -9: "MP_ERR_TIMEOUT"}
+
+
+class MPError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__("%s failed: %s (%s)" % (what, ERRORS.get(code, code), _strerror(code)))
+
+
+class mp_model_desc(ctypes.Structure):
+    _fields_ = [("n_species", ctypes.c_int32), ("F", ctypes.c_int32), ("lmax", ctypes.c_int32),
+                ("n_layers_full", ctypes.c_int32), ("H", ctypes.c_int32),
+                ("n_basis", ctypes.c_int32), ("p_env", ctypes.c_int32),
+                ("head_hidden", ctypes.c_int32), ("r_cut", ctypes.c_double),
+                ("n_avg", ctypes.c_double), ("rep_eps", ctypes.c_double),
+                ("rep_sigma", ctypes.c_double)]
+
+
+class mp_md_opts(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("n_parts", ctypes.c_int32), ("k_hops", ctypes.c_int32),
+                ("halo_mode", ctypes.c_int32), ("use_head", ctypes.c_int32),
+                ("forces_valid", ctypes.c_int32), ("check_every", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libmpip.so is not built (run paper_2509_21694_gb300/build.py)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "mp_weights_count": (I32, [ctypes.POINTER(mp_model_desc), ctypes.POINTER(I64)]),
+        "mp_create": (I32, [PP, ctypes.POINTER(mp_model_desc), P, I64, P]),
+        "mp_set_stream": (I32, [P, P]),
+        "mp_set_head": (I32, [P, P, I64]),
+        "mp_destroy": (None, [P]),
+        "mp_build_neighbors": (I32, [P, P, I64, ctypes.POINTER(D), PP]),
+        "mp_graph_info": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "mp_graph_export": (I32, [P, P, P, P]),
+        "mp_graph_free": (None, [P]),
+        "mp_partition": (I32, [P, P, I32, I32, I32, PP, ctypes.POINTER(D)]),
+        "mp_plan_info": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64),
+                               ctypes.POINTER(I64)]),
+        "mp_plan_export": (I32, [P, I32, P, P]),
+        "mp_plan_free": (None, [P]),
+        "mp_energy_forces": (I32, [P, P, P, P, P, I32, I32, I32, P, P, P]),
+        "mp_md_step": (I32, [P, P, P, P, P, P, I64, ctypes.POINTER(D), D, I32,
+                             ctypes.POINTER(mp_md_opts), P]),
+        "mp_strerror": (ctypes.c_char_p, [I32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _strerror(code: int) -> str:
+    return _lib.mp_strerror(code).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != MP_OK:
+        raise MPError(rc, what)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ---------------------------------------------------------------- weights --
+
+def desc_struct(desc) -> mp_model_desc:
+    return mp_model_desc(desc.n_species, desc.F, desc.lmax, desc.n_layers_full, desc.H,
+                         desc.n_basis, desc.p_env, desc.head_hidden, desc.r_cut, desc.n_avg,
+                         desc.rep_eps, desc.rep_sigma)
+
+
+def head_vector(w: dict) -> np.ndarray:
+    return np.concatenate([np.ravel(w[k]) for k in ("head_W1", "head_b1", "head_W2", "head_b2")])
+
+
+def pack_weights(w: dict, desc) -> np.ndarray:
+    """Flat float64 vector in the order mp_create documents."""
+    parts = [w["emb"], w["e0"], w["w_out"], head_vector(w)]
+    for t in range(desc.n_layers_full):
+        parts += [w["W1"][t], w["W2"][t], w["W3"][t], w["W0"][t], w["U1"][t]]
+        if desc.lmax >= 2:
+            parts.append(w["U2"][t])
+        parts += [w["b"][t], w["V1"][t]]
+        if desc.lmax >= 2:
+            parts.append(w["V2"][t])
+    out = np.ascontiguousarray(np.concatenate([np.ravel(np.asarray(p, np.float64)) for p in parts]))
+    n = ctypes.c_int64()
+    _check(_lib.mp_weights_count(ctypes.byref(desc_struct(desc)), ctypes.byref(n)), "mp_weights_count")
+    if out.size != n.value:
+        raise ValueError("weight vector has %d entries, expected %d" % (out.size, n.value))
+    return out
+
+
+# --------------------------------------------------------- C-named calls --
+
+def mp_create(desc, weights: dict, stream: int | None = None) -> int:
+    vec = pack_weights(weights, desc)
+    h = ctypes.c_void_p()
+    ds = desc_struct(desc)
+    _check(_lib.mp_create(ctypes.byref(h), ctypes.byref(ds), vec.ctypes.data, vec.size,
+                          _stream() if stream is None else stream), "mp_create")
+    return h.value
+
+
+def mp_destroy(ctx: int):
+    _lib.mp_destroy(ctx)
+
+
+def mp_set_stream(ctx: int, stream: int):
+    _check(_lib.mp_set_stream(ctx, stream), "mp_set_stream")
+
+
+def mp_set_head(ctx: int, head: np.ndarray):
+    head = np.ascontiguousarray(head, dtype=np.float64)
+    _check(_lib.mp_set_head(ctx, head.ctypes.data, head.size), "mp_set_head")
+
+
+def mp_build_neighbors(ctx: int, pos: torch.Tensor, box) -> int:
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    g = ctypes.c_void_p()
+    _check(_lib.mp_build_neighbors(ctx, _ptr(pos), pos.shape[0], b, ctypes.byref(g)),
+           "mp_build_neighbors")
+    return g.value
+
+
+def mp_graph_info(g: int):
+    n, e = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.mp_graph_info(g, ctypes.byref(n), ctypes.byref(e)), "mp_graph_info")
+    return n.value, e.value
+
+
+def mp_graph_export(g: int):
+    n, ne = mp_graph_info(g)
+    dev = torch.device("cuda")
+    recv = torch.empty(ne, dtype=torch.int32, device=dev)
+    send = torch.empty(ne, dtype=torch.int32, device=dev)
+    shift = torch.empty(ne, dtype=torch.int8, device=dev)
+    if ne:
+        _check(_lib.mp_graph_export(g, _ptr(recv), _ptr(send), _ptr(shift)), "mp_graph_export")
+    return recv, send, shift
+
+
+def mp_graph_free(g: int):
+    _lib.mp_graph_free(g)
+
+
+def mp_partition(ctx: int, g: int, n_parts: int, k_hops: int, mode: int = MP_HALO_GEOM):
+    p = ctypes.c_void_p()
+    H = ctypes.c_double()
+    _check(_lib.mp_partition(ctx, g, n_parts, k_hops, mode, ctypes.byref(p), ctypes.byref(H)),
+           "mp_partition")
+    return p.value, H.value
+
+
+def mp_plan_info(plan: int, p: int):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.mp_plan_info(plan, p, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "mp_plan_info")
+    return a.value, b.value, c.value
+
+
+def mp_plan_export(plan: int, p: int):
+    n_ext, _, _ = mp_plan_info(plan, p)
+    gid = torch.empty(max(n_ext, 1), dtype=torch.int32, device="cuda")
+    root = torch.empty(max(n_ext, 1), dtype=torch.uint8, device="cuda")
+    _check(_lib.mp_plan_export(plan, p, _ptr(gid), _ptr(root)), "mp_plan_export")
+    return gid[:n_ext], root[:n_ext]
+
+
+def mp_plan_free(plan: int):
+    _lib.mp_plan_free(plan)
+
+
+def mp_energy_forces(ctx: int, pos: torch.Tensor, species: torch.Tensor, g: int, plan,
+                     n_layers: int, precision: int = MP_FP32, use_head: bool = False,
+                     energy: torch.Tensor | None = None, forces: torch.Tensor | None = None,
+                     e_atom: torch.Tensor | None = None):
+    n = pos.shape[0]
+    if energy is None:
+        energy = torch.empty(1, dtype=torch.float64, device=pos.device)
+    if forces is None:
+        forces = torch.empty(n, 3, dtype=torch.float32, device=pos.device)
+    _check(_lib.mp_energy_forces(ctx, _ptr(pos), _ptr(species), g, plan or None, n_layers,
+                                 precision, int(use_head), _ptr(energy), _ptr(forces),
+                                 _ptr(e_atom)), "mp_energy_forces")
+    return energy, forces, e_atom
+
+
+def mp_md_step(ctx: int, pos, vel, forces, mass, species, box, dt: float, n_steps: int,
+               n_layers: int, precision: int = MP_FP32, n_parts: int = 1, k_hops: int = 0,
+               halo_mode: int = MP_HALO_GEOM, use_head: bool = False, forces_valid: bool = False,
+               check_every: int = 0, ledger: bool = True):
+    opts = mp_md_opts(n_layers, precision, n_parts, k_hops, halo_mode, int(use_head),
+                      int(forces_valid), check_every)
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    led = np.zeros((max(n_steps, 1), 3), dtype=np.float64)
+    _check(_lib.mp_md_step(ctx, _ptr(pos), _ptr(vel), _ptr(forces), _ptr(mass), _ptr(species),
+                           pos.shape[0], b, dt, n_steps, ctypes.byref(opts),
+                           led.ctypes.data if ledger else None), "mp_md_step")
+    return led[:n_steps]
+
+
+def mp_strerror(code: int) -> str:
+    return _strerror(code)
+
+
+# ------------------------------------------------------- object wrapper --
+
+class Potential:
+    """Owns an mp_ctx for one model on the current CUDA device and stream."""
+
+    def __init__(self, desc, weights: dict):
+        self.desc = desc
+        self.ctx = mp_create(desc, weights)
+
+    def close(self):
+        if self.ctx:
+            mp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def energy_forces(self, pos, species, box, n_layers, precision=MP_FP32, n_parts=1,
+                      k_hops=None, halo_mode=MP_HALO_GEOM, use_head=False, per_atom=False):
+        """Neighbours, optional partition plan and E/F in one call."""
+        mp_set_stream(self.ctx, _stream())
+        g = mp_build_neighbors(self.ctx, pos, box)
+        plan = None
+        try:
+            if n_parts > 1:
+                plan, _ = mp_partition(self.ctx, g, n_parts,
+                                       n_layers if k_hops is None else k_hops, halo_mode)
+            e_atom = (torch.empty(pos.shape[0], dtype=torch.float64, device=pos.device)
+                      if per_atom else None)
+            E, F, e_atom = mp_energy_forces(self.ctx, pos, species, g, plan, n_layers, precision,
+                                            use_head, e_atom=e_atom)
+        finally:
+            if plan:
+                mp_plan_free(plan)
+            mp_graph_free(g)
+        return E, F, e_atom
+
+
+class EnergyForces(torch.autograd.Function):
+    """E(pos) as an autograd node: backward returns -F * grad_output from the
+    library's hand-written adjoint (no torch autograd through the network)."""
+
+    @staticmethod
+    def forward(ctx, pos, potential, species, box, n_layers, precision):
+        E, F, _ = potential.energy_forces(pos.detach(), species, box, n_layers, precision)
+        ctx.save_for_backward(F)
+        return E[0]
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (F,) = ctx.saved_tensors
+        return -F.to(torch.float64) * grad_out, None, None, None, None, None

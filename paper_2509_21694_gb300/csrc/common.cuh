@@ -1,0 +1,155 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+
+#include "mpip.h"
+
+namespace mp {
+
+constexpr int kH = 64;        // radial MLP hidden width
+constexpr int kNB = 8;        // Bessel functions
+constexpr int kHeadH = 32;    // correction-head hidden width
+constexpr double kKappa = 9.648533212e-3;   // eV/(A amu) -> A/fs^2
+
+#define MP_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return MP_ERR_CUDA;          \
+    } while (0)
+
+#define MP_TRY(expr)                                        \
+    do {                                                    \
+        int _rc = (expr);                                   \
+        if (_rc != MP_OK) return _rc;                       \
+    } while (0)
+
+// Grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    int reserve(size_t nbytes);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Device copies of one layer's weights.  *T arrays are transposed
+// ([in][out]) so that a thread owning an output channel reads coalesced.
+struct LayerW {
+    float* W1;     // [H][NB]
+    float* W2;     // [H][H]   (out, in)
+    float* W2T;    // [H][H]   (in, out)
+    float* W3;     // [P][H]
+    float* W3T;    // [H][P]
+    float* W0;     // [F][F]  (out, in)
+    float* W0T;
+    float* U[2];   // U1, U2 (out, in)
+    float* UT[2];
+    float* b;      // [F]
+    float* V[2];   // V1, V2 (out, in)
+    float* VT[2];
+    // BF16 operand copies for the tensor-core path
+    __nv_bfloat16* W2b;    // [H][H]   (out, in), K-major
+    __nv_bfloat16* W3b;    // [P][H]   K-major
+    __nv_bfloat16* W3Tb;   // [H][P]   (backward operand, K = P)
+    __nv_bfloat16* W2Tb;   // [H][H]   (in, out)
+};
+
+struct Model {
+    mp_model_desc d;
+    int P = 0;      // radial outputs F (1 + 2 lmax)
+    int NLM = 0;    // (lmax + 1)^2
+    float* emb = nullptr;      // [S][F]
+    float* e0 = nullptr;       // [S]
+    float* w_out = nullptr;    // [F]
+    float* head = nullptr;     // W1[Hh][F], b1[Hh], W2[Hh], b2[1] contiguous
+    std::vector<LayerW> layers;
+    DevBuf store;              // owns every array above
+};
+
+// Neighbour graph in cell order.  perm[s] = caller id of sorted atom s.
+struct Graph {
+    int64_t n = 0, n_edges = 0;
+    double box[3];
+    int nc[3];
+    DevBuf perm, inv, xs, cell_start, row_ptr, col, shift, scratch;
+};
+
+struct Part {
+    int64_t n_ext = 0, n_root = 0, n_edges = 0;
+    DevBuf gid;       // int32 [n_ext]  sorted-global ids
+    DevBuf is_root;   // uint8 [n_ext]
+    DevBuf row_ptr;   // int64 [n_ext + 1]
+    DevBuf col;       // int32 [n_edges]  local ids
+    DevBuf shift;     // int8  [n_edges]
+};
+
+struct Plan {
+    int n_parts = 0, k_hops = 0, mode = 0;
+    int64_t n = 0;
+    std::vector<Part> parts;
+};
+
+// Views of one sub-system (whole graph or one partition) for the evaluator.
+struct SubSys {
+    int64_t n;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const int8_t* shift;
+    const int32_t* gid;       // local -> sorted-global id, nullptr = identity
+    const uint8_t* is_root;   // nullptr = all roots
+};
+
+struct Workspace {
+    DevBuf xl, sp, H, A, S, G0, G1, alpha, floc, eatom, esum, fsum, ebuf,
+        err, tmp, xw, perm_pos, pscr, red;
+};
+
+}  // namespace mp
+
+struct mp_ctx {
+    mp::Model model;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    mp::Workspace ws;
+    int* h_err = nullptr;      // pinned host word for error read-back
+};
+
+struct mp_graph {
+    mp::Graph g;
+    mp_ctx* ctx;
+};
+
+struct mp_plan {
+    mp::Plan p;
+    mp_ctx* ctx;
+    const mp_graph* graph;     // the graph the plan was built from (not owned)
+};
+
+namespace mp {
+
+// neighbors.cu
+int build_graph(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3], Graph& g);
+// partition.cu
+int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, Plan& plan,
+               double* halo_factor);
+// evaluate.cu
+int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,
+             const Plan* plan, int n_layers, int precision, int use_head, double* d_energy,
+             float* d_forces, double* d_e_atom);
+// scan.cu
+int exclusive_scan_i64(const int32_t* in, int64_t* out, int64_t n, DevBuf& tmp, cudaStream_t s);
+int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, DevBuf& tmp, cudaStream_t s);
+// md.cu
+int md_run(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const double* d_mass,
+           const int32_t* d_species, int64_t n, const double box[3], double dt, int n_steps,
+           const mp_md_opts* o, double* h_ledger);
+
+inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
+
+}  // namespace mp

@@ -1,0 +1,400 @@
+// Energy and forces of the first K layers (the pruned model), whole graph or
+// partition by partition.
+//
+// Per sub-system (the whole graph, or one partition's extended set with its
+// local CSR): embedding -> K x (edge forward, node update) -> readout
+// E_i = w_out . h0^(K) + e0[z_i] (+ head) (+ pair term) -> adjoint seeded
+// with s_i (1 on roots, 0 on halo atoms) -> K x (node adjoint, edge
+// adjoint) accumulating F.  Partition results are combined in partition
+// order: root energies are written once each, forces are summed (Methods,
+// "Global Output Integration": E = sum of root energies, F = sum over
+// partitions of the gradients of root energies).
+#include "kernels.h"
+
+namespace mp {
+
+namespace {
+
+__global__ void k_gather_pos(const double* __restrict__ pos, const int32_t* __restrict__ species,
+                             const int32_t* __restrict__ perm, int64_t n, double L0, double L1,
+                             double L2, double* __restrict__ xs, int32_t* __restrict__ sp) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t i = perm[s];
+    const double L[3] = {L0, L1, L2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double x = pos[3 * i + a];
+        double w = __dsub_rn(x, __dmul_rn(L[a], floor(__ddiv_rn(x, L[a]))));
+        if (w >= L[a]) w = __dsub_rn(w, L[a]);
+        xs[3 * s + a] = w;
+    }
+    sp[s] = species[i];
+}
+
+__global__ void k_gather_local(const int32_t* __restrict__ gid, int64_t n,
+                               const double* __restrict__ xs, const int32_t* __restrict__ sp,
+                               double* __restrict__ xl, int32_t* __restrict__ spl) {
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const int64_t s = gid[l];
+    xl[3 * l] = xs[3 * s];
+    xl[3 * l + 1] = xs[3 * s + 1];
+    xl[3 * l + 2] = xs[3 * s + 2];
+    spl[l] = sp[s];
+}
+
+__global__ void k_embed(const int32_t* __restrict__ sp, int64_t n, int F, int NLM,
+                        const float* __restrict__ emb, float* __restrict__ H) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t total = n * NLM * F;
+    if (idx >= total) return;
+    const int c = (int)(idx % F);
+    const int q = (int)((idx / F) % NLM);
+    const int64_t i = idx / ((int64_t)F * NLM);
+    H[idx] = q == 0 ? emb[(int64_t)sp[i] * F + c] : 0.f;
+}
+
+// Readout and adjoint seed: E_i = w_out . h0 + e0[z] (+ head), warp per atom.
+// The head E^head_i = W2 . silu(W1 h0 + b1) + b2 has hidden width 32 = one
+// lane per hidden unit.  G0 = s_i (w_out + dE^head/dh0); higher l: 0.
+__global__ void k_readout(int64_t n, int F, int NLM, const float* __restrict__ H,
+                          const int32_t* __restrict__ sp, const float* __restrict__ w_out,
+                          const float* __restrict__ e0, const float* __restrict__ head,
+                          const uint8_t* __restrict__ seed, double* __restrict__ Ei,
+                          float* __restrict__ G) {
+    extern __shared__ float sh_h[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (i >= n) return;
+    float* h = sh_h + wib * F;
+    const float* hi = H + (i * NLM) * F;
+    float e = 0.f;
+    for (int c = lane; c < F; c += 32) {
+        h[c] = hi[c];
+        e = fmaf(w_out[c], h[c], e);
+    }
+    __syncwarp();
+    float gk = 0.f, eh = 0.f;
+    if (head) {
+        const float* W1 = head;
+        const float* b1 = head + kHeadH * F;
+        const float* W2 = b1 + kHeadH;
+        float z = b1[lane];
+        for (int c = 0; c < F; ++c) z = fmaf(W1[lane * F + c], h[c], z);
+        eh = W2[lane] * silu(z);
+        gk = W2[lane] * silu_grad(z);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        eh += __shfl_xor_sync(0xffffffffu, eh, o);
+    }
+    const float s = seed ? (float)seed[i] : 1.f;
+    for (int c = lane; c < F; c += 32) {
+        float g = w_out[c];
+        if (head) {
+            for (int k = 0; k < kHeadH; ++k)
+                g = fmaf(head[k * F + c], __shfl_sync(0xffffffffu, gk, k), g);
+        }
+        G[(i * NLM) * F + c] = s * g;
+        for (int q = 1; q < NLM; ++q) G[(i * NLM + q) * F + c] = 0.f;
+    }
+    if (lane == 0) {
+        double v = (double)e + (double)e0[sp[i]];
+        if (head) v += (double)eh + (double)head[kHeadH * F + 2 * kHeadH];
+        Ei[i] = v;
+    }
+}
+
+// Pair term phi(r) = eps (sigma/r)^12 u(r/r_c): E_i += 1/2 sum_row phi and
+// F_k += sum_i 1/2 (s_k + s_i) phi'(r) u_hat (both directed edges of a pair
+// carry half of phi).  Warp per row.
+__global__ void k_pair_term(int64_t n, const int64_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ col, const int8_t* __restrict__ shift,
+                            const double* __restrict__ x, EdgeConst k,
+                            const uint8_t* __restrict__ seed, double* __restrict__ Ei,
+                            double* __restrict__ frc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    float ei = 0.f, f[3] = {0.f, 0.f, 0.f};
+    const float si = seed ? (float)seed[i] : 1.f;
+    for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
+        const int j = col[e];
+        float d[3];
+        edge_vector(x, i, j, shift[e], k, d);
+        const float r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        float u, du;
+        envelope(r, k, u, du);
+        const float ir = 1.f / r, ir2 = ir * ir, ir4 = ir2 * ir2;
+        const float s12 = k.rep_sig12 * ir4 * ir4 * ir4;
+        ei += 0.5f * k.rep_eps * s12 * u;
+        const float dphi = k.rep_eps * s12 * (du - 12.f * ir * u);
+        const float sj = seed ? (float)seed[j] : 1.f;
+        const float g = 0.5f * (si + sj) * dphi * ir;
+        f[0] += g * d[0];
+        f[1] += g * d[1];
+        f[2] += g * d[2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ei += __shfl_xor_sync(0xffffffffu, ei, o);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
+    }
+    if (lane == 0) {
+        Ei[i] += (double)ei;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) frc[3 * i + q] += (double)f[q];
+    }
+}
+
+__global__ void k_scatter(int64_t n, const int32_t* __restrict__ gid,
+                          const uint8_t* __restrict__ is_root, const double* __restrict__ Ei,
+                          const double* __restrict__ floc, double* __restrict__ e_sorted,
+                          double* __restrict__ f_sorted) {
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const int64_t s = gid ? gid[l] : l;
+    if (!is_root || is_root[l]) e_sorted[s] = Ei[l];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) f_sorted[3 * s + q] += floc[3 * l + q];
+}
+
+__global__ void k_finalize(int64_t n, const int32_t* __restrict__ perm,
+                           const double* __restrict__ e_sorted, const double* __restrict__ f_sorted,
+                           float* __restrict__ forces, double* __restrict__ e_atom) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t i = perm[s];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) forces[3 * i + q] = (float)f_sorted[3 * s + q];
+    if (e_atom) e_atom[i] = e_sorted[s];
+}
+
+// Deterministic FP64 sum: fixed per-block tree, then one block over partials.
+constexpr int kRedThreads = 256;
+constexpr int kRedItems = 8;
+
+__global__ void k_sum_partial(const double* __restrict__ v, int64_t n, double* __restrict__ part) {
+    __shared__ double sm[kRedThreads];
+    const int64_t base = (int64_t)blockIdx.x * kRedThreads * kRedItems;
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < kRedItems; ++q) {
+        const int64_t idx = base + (int64_t)q * kRedThreads + threadIdx.x;
+        if (idx < n) acc += v[idx];
+    }
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+__global__ void k_sum_final(const double* __restrict__ part, int64_t m, double* __restrict__ out) {
+    __shared__ double sm[kRedThreads];
+    double acc = 0.0;
+    for (int64_t idx = threadIdx.x; idx < m; idx += kRedThreads) acc += part[idx];
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sm[0];
+}
+
+}  // namespace
+
+int reduce_sum(const double* v, int64_t n, double* out, DevBuf& tmp, cudaStream_t st) {
+    const int64_t per = (int64_t)kRedThreads * kRedItems;
+    const int64_t blocks = n > 0 ? (n + per - 1) / per : 1;
+    MP_TRY(tmp.reserve(sizeof(double) * blocks));
+    if (n > 0)
+        k_sum_partial<<<(unsigned)blocks, kRedThreads, 0, st>>>(v, n, tmp.as<double>());
+    else
+        MP_CUDA_TRY(cudaMemsetAsync(tmp.as<double>(), 0, sizeof(double), st));
+    k_sum_final<<<1, kRedThreads, 0, st>>>(tmp.as<double>(), blocks, out);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+namespace {
+
+struct EvalBufs {
+    double* xs;       // sorted wrapped positions
+    int32_t* sp;      // sorted species
+    double* e_sorted;
+    double* f_sorted;
+    double* xl;
+    int32_t* spl;
+    float* H;         // (K+1) feature arrays
+    float* A;         // K message arrays
+    float* S;         // K pre-activation arrays
+    float* alpha;
+    float* G[2];
+    double* floc;
+    double* eloc;
+};
+
+int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeConst& kc, int K,
+                  int precision, int use_head) {
+    const Model& m = ctx->model;
+    cudaStream_t st = ctx->stream;
+    const int F = m.d.F, NLM = m.NLM;
+    const int64_t n = ss.n;
+    if (n == 0) return MP_OK;
+    const int64_t feat = n * NLM * F;
+    const double* x = b.xs;
+    const int32_t* sp = b.sp;
+    if (ss.gid) {
+        k_gather_local<<<grid_for(n, 256), 256, 0, st>>>(ss.gid, n, b.xs, b.sp, b.xl, b.spl);
+        x = b.xl;
+        sp = b.spl;
+    }
+    k_embed<<<grid_for(feat, 256), 256, 0, st>>>(sp, n, F, NLM, m.emb, b.H);
+    EdgeArgs ea{};
+    ea.n = n;
+    ea.row_ptr = ss.row_ptr;
+    ea.col = ss.col;
+    ea.shift = ss.shift;
+    ea.x = x;
+    ea.k = kc;
+    ea.seed = ss.is_root;
+    NodeArgs na{};
+    na.n = n;
+    na.inv_navg = kc.inv_navg;
+    for (int t = 0; t < K; ++t) {
+        ea.w = &m.layers[t];
+        ea.first = t == 0;
+        ea.Hin = b.H + t * feat;
+        ea.Aout = b.A + t * feat;
+        if (precision == MP_BF16)
+            MP_TRY(launch_edge_fwd_bf16(m, ea, st, ctx->num_sms));
+        else
+            MP_TRY(launch_edge_fwd_f32(m, ea, st));
+        na.w = &m.layers[t];
+        na.A = b.A + t * feat;
+        na.Hin = b.H + t * feat;
+        na.Hout = b.H + (t + 1) * feat;
+        na.S = b.S + t * n * F;
+        na.last = t == K - 1;
+        MP_TRY(launch_node_fwd_f32(m, na, st));
+    }
+    {
+        const int wpb = 4;
+        k_readout<<<grid_for(n, wpb), 32 * wpb, sizeof(float) * F * wpb, st>>>(
+            n, F, NLM, b.H + (int64_t)K * feat, sp, m.w_out, m.e0, use_head ? m.head : nullptr,
+            ss.is_root, b.eloc, b.G[K & 1]);
+    }
+    MP_CUDA_TRY(cudaMemsetAsync(b.floc, 0, sizeof(double) * 3 * n, st));
+    if (m.d.rep_eps != 0.0) {
+        const int wpb = 8;
+        k_pair_term<<<grid_for(n, wpb), 32 * wpb, 0, st>>>(n, ss.row_ptr, ss.col, ss.shift, x, kc,
+                                                           ss.is_root, b.eloc, b.floc);
+    }
+    for (int t = K - 1; t >= 0; --t) {
+        float* Gout = b.G[(t + 1) & 1];
+        float* Gin = b.G[t & 1];
+        na.w = &m.layers[t];
+        na.A = b.A + t * feat;
+        na.S = b.S + t * n * F;
+        na.Gout = Gout;
+        na.Alpha = b.alpha;
+        na.last = t == K - 1;
+        MP_TRY(launch_node_bwd_f32(m, na, st));
+        ea.w = &m.layers[t];
+        ea.first = t == 0;
+        ea.Hin = b.H + t * feat;
+        ea.Alpha = b.alpha;
+        ea.Gout = Gout;
+        ea.Gin = t == 0 ? nullptr : Gin;
+        ea.frc = b.floc;
+        if (precision == MP_BF16)
+            MP_TRY(launch_edge_bwd_bf16(m, ea, st, ctx->num_sms));
+        else
+            MP_TRY(launch_edge_bwd_f32(m, ea, st));
+    }
+    k_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, ss.gid, ss.is_root, b.eloc, b.floc, b.e_sorted,
+                                                b.f_sorted);
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+}  // namespace
+
+int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,
+             const Plan* plan, int K, int precision, int use_head, double* d_energy,
+             float* d_forces, double* d_e_atom) {
+    const Model& m = ctx->model;
+    if (!d_pos || !d_species || !d_energy || !d_forces) return MP_ERR_ARG;
+    if (K < 0 || K > m.d.n_layers_full) return MP_ERR_ARG;
+    if (precision != MP_FP32 && precision != MP_BF16) return MP_ERR_ARG;
+    if (plan && plan->n != g.n) return MP_ERR_ARG;
+    cudaStream_t st = ctx->stream;
+    Workspace& ws = ctx->ws;
+    const int64_t n = g.n;
+    const int F = m.d.F, NLM = m.NLM;
+
+    std::vector<SubSys> subs;
+    if (!plan) {
+        subs.push_back(SubSys{n, g.row_ptr.as<int64_t>(), g.col.as<int32_t>(),
+                              g.shift.as<int8_t>(), nullptr, nullptr});
+    } else {
+        for (const Part& P : plan->parts)
+            subs.push_back(SubSys{P.n_ext, P.row_ptr.as<int64_t>(), P.col.as<int32_t>(),
+                                  P.shift.as<int8_t>(), P.gid.as<int32_t>(),
+                                  P.is_root.as<uint8_t>()});
+    }
+    int64_t nmax = 0;
+    for (const SubSys& s : subs) nmax = s.n > nmax ? s.n : nmax;
+    const int64_t feat = nmax * NLM * F;
+
+    MP_TRY(ws.xw.reserve(sizeof(double) * 3 * n));
+    MP_TRY(ws.sp.reserve(sizeof(int32_t) * 2 * n + 64));
+    MP_TRY(ws.esum.reserve(sizeof(double) * n));
+    MP_TRY(ws.fsum.reserve(sizeof(double) * 3 * n));
+    MP_TRY(ws.xl.reserve(sizeof(double) * 3 * nmax + sizeof(int32_t) * nmax + 64));
+    MP_TRY(ws.H.reserve(sizeof(float) * (K + 1) * feat));
+    MP_TRY(ws.A.reserve(sizeof(float) * (K > 0 ? K : 1) * feat));
+    MP_TRY(ws.S.reserve(sizeof(float) * (K > 0 ? K : 1) * nmax * F));
+    MP_TRY(ws.alpha.reserve(sizeof(float) * feat));
+    MP_TRY(ws.G0.reserve(sizeof(float) * feat));
+    MP_TRY(ws.G1.reserve(sizeof(float) * feat));
+    MP_TRY(ws.floc.reserve(sizeof(double) * 3 * nmax));
+    MP_TRY(ws.eatom.reserve(sizeof(double) * nmax));
+
+    EvalBufs b;
+    b.xs = ws.xw.as<double>();
+    b.sp = ws.sp.as<int32_t>();
+    b.e_sorted = ws.esum.as<double>();
+    b.f_sorted = ws.fsum.as<double>();
+    b.xl = ws.xl.as<double>();
+    b.spl = reinterpret_cast<int32_t*>(b.xl + 3 * nmax);
+    b.H = ws.H.as<float>();
+    b.A = ws.A.as<float>();
+    b.S = ws.S.as<float>();
+    b.alpha = ws.alpha.as<float>();
+    b.G[0] = ws.G0.as<float>();
+    b.G[1] = ws.G1.as<float>();
+    b.floc = ws.floc.as<double>();
+    b.eloc = ws.eatom.as<double>();
+
+    k_gather_pos<<<grid_for(n, 256), 256, 0, st>>>(d_pos, d_species, g.perm.as<int32_t>(), n,
+                                                   g.box[0], g.box[1], g.box[2], b.xs, b.sp);
+    MP_CUDA_TRY(cudaMemsetAsync(b.f_sorted, 0, sizeof(double) * 3 * n, st));
+    MP_CUDA_TRY(cudaMemsetAsync(b.e_sorted, 0, sizeof(double) * n, st));
+    const EdgeConst kc = make_edge_const(m.d, g.box);
+    for (const SubSys& s : subs) MP_TRY(run_subsystem(ctx, s, b, kc, K, precision, use_head));
+    k_finalize<<<grid_for(n, 256), 256, 0, st>>>(n, g.perm.as<int32_t>(), b.e_sorted, b.f_sorted,
+                                                 d_forces, d_e_atom);
+    MP_TRY(reduce_sum(b.e_sorted, n, d_energy, ws.red, st));
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+}  // namespace mp

@@ -1,0 +1,50 @@
+// Launch interfaces of the evaluator's kernels.
+#pragma once
+
+#include "common.cuh"
+#include "edge_math.cuh"
+
+namespace mp {
+
+// One message-passing layer over a receiver-sorted CSR (local ids).
+struct EdgeArgs {
+    int64_t n;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const int8_t* shift;
+    const double* x;          // [n][3] wrapped positions
+    EdgeConst k;
+    const LayerW* w;
+    const float* Hin;         // [n][NLM][F] layer input features
+    float* Aout;              // forward: [n][NLM][F] aggregated messages (/N_avg)
+    const float* Alpha;       // adjoint: [n][NLM][F] dE/dA / N_avg
+    const float* Gout;        // adjoint: [n][NLM][F] dE/d(layer output)
+    float* Gin;               // adjoint: [n][NLM][F] dE/d(layer input); null at layer 0
+    const uint8_t* seed;      // adjoint: root flags (null = all 1)
+    double* frc;              // adjoint: [n][3] forces, accumulated
+    bool first;               // layer 0: input l >= 1 features are zero
+};
+
+int launch_edge_fwd_f32(const Model& m, const EdgeArgs& a, cudaStream_t st);
+int launch_edge_bwd_f32(const Model& m, const EdgeArgs& a, cudaStream_t st);
+int launch_edge_fwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int num_sms);
+int launch_edge_bwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int num_sms);
+
+// Node update of layer t: S = W0 A0 + sum_l Ul Bl + b; h0' = h0 + silu(S);
+// hl' = hl + Vl Al (skipped when last).
+struct NodeArgs {
+    int64_t n;
+    const LayerW* w;
+    const float* A;
+    const float* Hin;
+    float* Hout;
+    float* S;
+    const float* Gout;   // adjoint
+    float* Alpha;        // adjoint output (/N_avg)
+    float inv_navg;
+    bool last;
+};
+int launch_node_fwd_f32(const Model& m, const NodeArgs& a, cudaStream_t st);
+int launch_node_bwd_f32(const Model& m, const NodeArgs& a, cudaStream_t st);
+
+}  // namespace mp

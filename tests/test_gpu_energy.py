@@ -1,0 +1,126 @@
+"""GPU energy / forces (hand-written adjoint) against the FP64 oracle.
+
+FP32 gate (both ways of measuring written here): max |F - F_ref| <= 1e-5 *
+F_rms and |E - E_ref| <= 1e-6 * N * rms_i(E_i,ref); per-atom energies within
+1e-6 * rms_i(E_i,ref).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import model as om
+from oracle import neighbors as onb
+
+pytestmark = pytest.mark.gpu
+
+F32_FORCE = 1e-5
+F32_ENERGY = 1e-6
+
+
+def _gpu(mp, d, w, s, K, precision=0, per_atom=True, **kw):
+    pot = mp.Potential(d, w)
+    pos = torch.tensor(s.pos, device="cuda")
+    sp = torch.tensor(s.species, device="cuda")
+    E, F, Ei = pot.energy_forces(pos, sp, s.box, K, precision, per_atom=per_atom, **kw)
+    torch.cuda.synchronize()
+    out = (float(E.item()), F.cpu().numpy().astype(np.float64),
+           None if Ei is None else Ei.cpu().numpy())
+    pot.close()
+    return out
+
+
+def _ref(d, w, s, K):
+    e = onb.edges(s.pos, s.box, d.r_cut)
+    return om.energy_forces(s.pos, s.species, s.box, e, w, d, K)
+
+
+def _check(got, ref, n, ftol=F32_FORCE, etol=F32_ENERGY):
+    E, F, Ei = got
+    Er, Eir, Fr = ref
+    frms = np.sqrt((Fr ** 2).mean())
+    erms = np.sqrt((Eir ** 2).mean())
+    assert np.abs(F - Fr).max() <= ftol * frms, (np.abs(F - Fr).max() / frms)
+    assert abs(E - Er) <= etol * n * erms, (abs(E - Er) / (n * erms))
+    if Ei is not None:
+        assert np.abs(Ei - Eir).max() <= etol * erms * 10
+
+
+def test_c1_fp32(mp):
+    s, d = synth.cu_fcc_small(), synth.model_c1()
+    w = synth.make_weights(d, 0)
+    _check(_gpu(mp, d, w, s, 2), _ref(d, w, s, 2), len(s.pos))
+
+
+@pytest.mark.parametrize("K", [0, 1, 2, 3])
+def test_alloy_lmax2_depths_fp32(mp, K):
+    s = synth.alloy_fcc(cells=(4, 4, 4))
+    d = synth.model_alloy(n_layers_full=3)
+    w = synth.make_weights(d, 1)
+    _check(_gpu(mp, d, w, s, K), _ref(d, w, s, K), len(s.pos))
+
+
+def test_pair_repulsion_and_species_shift_fp32(mp):
+    s = synth.alloy_fcc(cells=(4, 4, 5), sigma=0.15, seed=6)
+    d = synth.model_alloy(n_layers_full=2)
+    d.rep_eps, d.rep_sigma = 0.8, 2.0
+    w = synth.make_weights(d, 2, {"e0": 1.0})
+    _check(_gpu(mp, d, w, s, 2), _ref(d, w, s, 2), len(s.pos))
+
+
+def test_c2_4000_atoms_pruned_fp32(mp):
+    s = synth.alloy_fcc()
+    d = synth.model_alloy(n_layers_full=6)
+    w = synth.make_weights(d, 1)
+    _check(_gpu(mp, d, w, s, 2), _ref(d, w, s, 2), len(s.pos))
+
+
+def test_full_depth_l6_fp32(mp):
+    s = synth.alloy_fcc(cells=(5, 5, 5), seed=5)
+    d = synth.model_alloy(n_layers_full=6)
+    w = synth.make_weights(d, 1)
+    _check(_gpu(mp, d, w, s, 6), _ref(d, w, s, 6), len(s.pos))
+
+
+def test_liquid_subcell_fp32(mp):
+    s = synth.liquid3(n=2000, seed=12)
+    d = synth.model_liquid(n_layers_full=2)
+    w = synth.make_weights(d, 2)
+    _check(_gpu(mp, d, w, s, 2), _ref(d, w, s, 2), len(s.pos))
+
+
+def test_isolated_atoms_and_empty_rows(mp):
+    # A sparse gas: many atoms without neighbours (empty CSR rows) between
+    # clustered ones; rows of 0, 1 and many edges inside one block.
+    rng = np.random.default_rng(4)
+    box = np.array([40.0, 40.0, 40.0])
+    pos = [rng.uniform(0, 40, 3) for _ in range(30)]
+    pos += [np.array([20.0, 20.0, 20.0]) + rng.normal(0, 1.2, 3) for _ in range(12)]
+    pos = np.array(pos)
+    s = synth.System(pos, box, np.zeros(len(pos), np.int32), np.full(len(pos), 63.5))
+    d = synth.model_alloy(n_layers_full=2)
+    d.rep_eps = 0.5
+    w = synth.make_weights(d, 3)
+    _check(_gpu(mp, d, w, s, 2), _ref(d, w, s, 2), len(s.pos))
+
+
+def test_autograd_function_matches(mp):
+    s, d = synth.cu_fcc_small(), synth.model_c1()
+    w = synth.make_weights(d, 0)
+    pot = mp.Potential(d, w)
+    pos = torch.tensor(s.pos, device="cuda", requires_grad=True)
+    E = mp.EnergyForces.apply(pos, pot, torch.tensor(s.species, device="cuda"), s.box, 2, 0)
+    E.backward()
+    _, _, Fr = _ref(d, w, s, 2)
+    frms = np.sqrt((Fr ** 2).mean())
+    assert np.abs(-pos.grad.cpu().numpy() - Fr).max() <= F32_FORCE * frms
+    pot.close()
+
+
+def test_deterministic_repeat(mp):
+    s = synth.alloy_fcc(cells=(4, 4, 4))
+    d = synth.model_alloy(n_layers_full=2)
+    w = synth.make_weights(d, 1)
+    a = _gpu(mp, d, w, s, 2)
+    b = _gpu(mp, d, w, s, 2)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])

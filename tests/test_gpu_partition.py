@@ -1,0 +1,87 @@
+"""GPU partitions: plan sets against the oracle (bit-exact), partitioned E/F
+against unpartitioned (<= 1e-6 F_rms) and against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import model as om
+from oracle import neighbors as onb
+from oracle import partition as op
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(mp, s, d, w):
+    pot = mp.Potential(d, w)
+    pos = torch.tensor(s.pos, device="cuda")
+    sp = torch.tensor(s.species, device="cuda")
+    return pot, pos, sp
+
+
+@pytest.mark.parametrize("P,K,mode", [(4, 2, 0), (4, 2, 1), (3, 1, 1), (5, 3, 0)])
+def test_plan_sets_match_oracle(mp, P, K, mode):
+    s = synth.alloy_fcc(cells=(5, 5, 12), sigma=0.1, seed=8)
+    d = synth.ModelDesc(n_species=2, F=64, lmax=1, n_layers_full=3, r_cut=4.0,
+                        n_avg=synth.n_avg_for(4.0, 4 / 3.6 ** 3))
+    w = synth.make_weights(d, 21)
+    pot, pos, sp = _setup(mp, s, d, w)
+    g = mp.mp_build_neighbors(pot.ctx, pos, s.box)
+    plan, H = mp.mp_partition(pot.ctx, g, P, K, mode)
+    e = onb.edges(s.pos, s.box, d.r_cut)
+    parts, Hr = op.plan(s.pos, s.box, e, P, K, d.r_cut, "geom" if mode == 0 else "bfs")
+    try:
+        for p, (roots, ext) in enumerate(parts):
+            gid, root = mp.mp_plan_export(plan, p)
+            gid = gid.cpu().numpy()
+            root = root.cpu().numpy().astype(bool)
+            got_ext = np.zeros(len(s.pos), bool)
+            got_ext[gid] = True
+            got_root = np.zeros(len(s.pos), bool)
+            got_root[gid[root]] = True
+            assert np.array_equal(got_ext, ext)
+            assert np.array_equal(got_root, roots)
+            n_ext, n_root, _ = mp.mp_plan_info(plan, p)
+            assert n_ext == ext.sum() and n_root == roots.sum()
+        assert abs(H - Hr) < 1e-12
+    finally:
+        mp.mp_plan_free(plan)
+        mp.mp_graph_free(g)
+        pot.close()
+
+
+@pytest.mark.parametrize("P,mode", [(4, 0), (4, 1), (6, 0)])
+def test_partitioned_equals_unpartitioned(mp, P, mode):
+    s = synth.alloy_fcc(cells=(6, 6, 16), sigma=0.1, seed=9)
+    d = synth.model_alloy(n_layers_full=2)
+    d.rep_eps = 0.3
+    w = synth.make_weights(d, 1)
+    pot, pos, sp = _setup(mp, s, d, w)
+    E0, F0, e0 = pot.energy_forces(pos, sp, s.box, 2, per_atom=True)
+    E1, F1, e1 = pot.energy_forces(pos, sp, s.box, 2, n_parts=P, halo_mode=mode, per_atom=True)
+    F0 = F0.cpu().numpy().astype(np.float64)
+    F1 = F1.cpu().numpy().astype(np.float64)
+    frms = np.sqrt((F0 ** 2).mean())
+    assert np.abs(F1 - F0).max() <= 1e-6 * frms, np.abs(F1 - F0).max() / frms
+    # root energies are computed from identical inputs in identical order
+    assert np.array_equal(e0.cpu().numpy(), e1.cpu().numpy())
+    assert abs(E1.item() - E0.item()) <= 1e-9 * abs(E0.item())
+    # and both agree with the FP64 oracle
+    Er, _, Fr = om.energy_forces(s.pos, s.species, s.box, onb.edges(s.pos, s.box, d.r_cut),
+                                 w, d, 2)
+    assert np.abs(F1 - Fr).max() <= 1e-5 * np.sqrt((Fr ** 2).mean())
+    pot.close()
+
+
+def test_truncated_halo_is_detected(mp):
+    # K-hop BFS with one hop too few must not reproduce the forces (so the
+    # equality test above has teeth on the GPU path too).
+    s = synth.alloy_fcc(cells=(6, 6, 16), sigma=0.1, seed=9)
+    d = synth.model_alloy(n_layers_full=2)
+    w = synth.make_weights(d, 1)
+    pot, pos, sp = _setup(mp, s, d, w)
+    _, F0, _ = pot.energy_forces(pos, sp, s.box, 2)
+    _, F1, _ = pot.energy_forces(pos, sp, s.box, 2, n_parts=4, k_hops=1, halo_mode=1)
+    F0 = F0.cpu().numpy()
+    assert np.abs(F1.cpu().numpy() - F0).max() > 1e-4 * np.sqrt((F0 ** 2).mean())
+    pot.close()
