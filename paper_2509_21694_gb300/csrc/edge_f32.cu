@@ -220,26 +220,57 @@ struct BwdSmem {
     float deps[CE][kNB];
     float Y[CE][NLM];
     float u[CE][4];          // unit vector, r
-    float a1[kH][CE], sp1[kH][CE], a2[kH][CE], sp2[kH][CE];
+    float a1[kH][CE], da1[kH][CE], a2[kH][CE], da2[kH][CE];
     float gR[P][CE + 1];
-    float gY[NW][CE][NLM];
-    float gz2[CE][kH], gz1[CE][kH];
-    float gd[CE][3];
+    double gY[NW][CE][NLM];
+    double gr[NW][CE];
     double frow[RPB][3];
     int row[CE], col[CE];
     int64_t rp[RPB + 1];
 };
 
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// a2 = silu(W2 a1) and its r-derivative da2 = silu'(z2) W2 da1 (forward mode).
+template <int F>
+__device__ __forceinline__ void hidden2_tangent(const float* __restrict__ W2T,
+                                                const float (*s_a1)[CE], const float (*s_da1)[CE],
+                                                float (*s_a2)[CE], float (*s_da2)[CE], int c) {
+    constexpr int EG = CE * kH / F;
+    const int kk = c % kH, e0 = (c / kH) * EG;
+    float z[EG], dz[EG];
+#pragma unroll
+    for (int q = 0; q < EG; ++q) z[q] = dz[q] = 0.f;
+#pragma unroll 4
+    for (int jj = 0; jj < kH; ++jj) {
+        const float wv = __ldg(&W2T[jj * kH + kk]);
+#pragma unroll
+        for (int q = 0; q < EG; ++q) {
+            z[q] = fmaf(wv, s_a1[jj][e0 + q], z[q]);
+            dz[q] = fmaf(wv, s_da1[jj][e0 + q], dz[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < EG; ++q) {
+        s_a2[kk][e0 + q] = silu(z[q]);
+        s_da2[kk][e0 + q] = silu_grad(z[q]) * dz[q];
+    }
+}
+
+// Adjoint of one layer.  dE/dr of an edge pair is obtained as
+// sum_q dE/dR_q * dR_q/dr with dR/dr propagated forward through the radial
+// MLP (it depends on the geometry only); the sums over channels run in FP64.
 template <int F, int LMAX, bool FIRST>
 __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restrict__ W1,
-                                                const float* __restrict__ W2,
                                                 const float* __restrict__ W2T,
-                                                const float* __restrict__ W3,
                                                 const float* __restrict__ W3T) {
     using PP = Paths<LMAX, FIRST>;
     using SM = BwdSmem<F, LMAX>;
-    constexpr int NLM = SM::NLM, P = SM::P;
-    constexpr int EG = CE * kH / F;
+    constexpr int NLM = SM::NLM;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM& s = *reinterpret_cast<SM*>(smem_raw);
 
@@ -303,14 +334,18 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
         __syncthreads();
         for (int o = c; o < kH * CE; o += F) {
             const int kk = o / CE, e = o % CE;
-            float z = 0.f;
+            float z = 0.f, dz = 0.f;
 #pragma unroll
-            for (int b = 0; b < kNB; ++b) z = fmaf(__ldg(&W1[kk * kNB + b]), s.eps[e][b], z);
+            for (int b = 0; b < kNB; ++b) {
+                const float wv = __ldg(&W1[kk * kNB + b]);
+                z = fmaf(wv, s.eps[e][b], z);
+                dz = fmaf(wv, s.deps[e][b], dz);
+            }
             s.a1[kk][e] = silu(z);
-            s.sp1[kk][e] = silu_grad(z);
+            s.da1[kk][e] = silu_grad(z) * dz;
         }
         __syncthreads();
-        hidden2<F, true>(W2T, s.a1, s.a2, s.sp2, c);
+        hidden2_tangent<F>(W2T, s.a1, s.da1, s.a2, s.da2, c);
         __syncthreads();
         float R[PP::NP][CE];
         radial_out<F, LMAX, FIRST>(W3T, s.a2, c, R);
@@ -366,7 +401,7 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
                 }
                 gacc[0] += g0;
             }
-            // (b) dE/dR for both directions; (c) dE/dY partial sums
+            // (b) dE/dR summed over both directions; (c) dE/dY partial sums
             s.gR[c][e] = ak[0] * hj[0] + aj[0] * hk[0];
             float gy[NLM];
             {
@@ -395,74 +430,43 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
             }
 #pragma unroll
             for (int q = 1; q < NLM; ++q) {
-                float v = gy[q];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                const double v = warp_sum_d((double)gy[q]);
                 if (lane == 0) s.gY[warp][e][q] = v;
             }
         }
-        __syncthreads();
-        // radial MLP transpose: ga2 = W3^T gR, gz2 = ga2 * silu'(z2)
-        {
-            const int kk = c % kH, e0 = (c / kH) * EG;
-            float z[EG];
+        // dR/dr for this thread's channel (same registers as R), contracted
+        // with dE/dR; the channel sum runs in FP64.
+        radial_out<F, LMAX, FIRST>(W3T, s.da2, c, R);
 #pragma unroll
-            for (int q = 0; q < EG; ++q) z[q] = 0.f;
-            for (int b = 0; b < 1 + 2 * LMAX; ++b) {
-                if (FIRST && b > 0 && (b & 1) == 0) continue;   // R_lb unused at layer 0
-                for (int pp = 0; pp < F; ++pp) {
-                    const int p = b * F + pp;
-                    const float wv = __ldg(&W3[p * kH + kk]);
+        for (int e = 0; e < CE; ++e) {
+            float part = 0.f;
 #pragma unroll
-                    for (int q = 0; q < EG; ++q) z[q] = fmaf(wv, s.gR[p][e0 + q], z[q]);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < EG; ++q) s.gz2[e0 + q][kk] = z[q] * s.sp2[kk][e0 + q];
-        }
-        __syncthreads();
-        {
-            const int kk = c % kH, e0 = (c / kH) * EG;
-            float z[EG];
-#pragma unroll
-            for (int q = 0; q < EG; ++q) z[q] = 0.f;
-#pragma unroll 4
-            for (int jj = 0; jj < kH; ++jj) {
-                const float wv = __ldg(&W2[jj * kH + kk]);
-#pragma unroll
-                for (int q = 0; q < EG; ++q) z[q] = fmaf(wv, s.gz2[e0 + q][jj], z[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < EG; ++q) s.gz1[e0 + q][kk] = z[q] * s.sp1[kk][e0 + q];
+            for (int q = 0; q < PP::NP; ++q) part = fmaf(s.gR[PP::block(q) * F + c][e], R[q][e], part);
+            const double v = warp_sum_d((double)part);
+            if (lane == 0) s.gr[warp][e] = v;
         }
         __syncthreads();
         if (c < CE && s.row[c] >= 0) {
             const int e = c;
-            float gr = 0.f;
+            double gr = 0.0, gY[NLM];
 #pragma unroll
-            for (int b = 0; b < kNB; ++b) {
-                float ge = 0.f;
-                for (int kk = 0; kk < kH; ++kk) ge = fmaf(__ldg(&W1[kk * kNB + b]), s.gz1[e][kk], ge);
-                gr = fmaf(ge, s.deps[e][b], gr);
-            }
-            float gY[NLM];
-            gY[0] = 0.f;
+            for (int w = 0; w < SM::NW; ++w) gr += s.gr[w][e];
+            gY[0] = 0.0;
 #pragma unroll
             for (int q = 1; q < NLM; ++q) {
-                float v = 0.f;
+                double v = 0.0;
 #pragma unroll
                 for (int w = 0; w < SM::NW; ++w) v += s.gY[w][e][q];
                 gY[q] = v;
             }
-            const float u[3] = {s.u[e][0], s.u[e][1], s.u[e][2]};
-            const float r = s.u[e][3];
-            float v[3];
-            sph_grad<LMAX>(u, gY, v);
-            const float vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
-            const float ir = 1.f / r;
-            const float radial = gr;
+            const double u[3] = {s.u[e][0], s.u[e][1], s.u[e][2]};
+            const double ir = 1.0 / (double)s.u[e][3];
+            double v[3];
+            sph_grad<LMAX, double>(u, gY, v);
+            const double vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
+            // row sums in a fixed order by one thread per chunk
 #pragma unroll
-            for (int q = 0; q < 3; ++q) s.gd[e][q] = radial * u[q] + (v[q] - vu * u[q]) * ir;
+            for (int q = 0; q < 3; ++q) s.gY[0][e][q] = gr * u[q] + (v[q] - vu * u[q]) * ir;
         }
         __syncthreads();
         if (c == 0) {
@@ -470,7 +474,7 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
                 const int lr = s.row[e];
                 if (lr < 0) break;
 #pragma unroll
-                for (int q = 0; q < 3; ++q) s.frow[lr][q] += (double)s.gd[e][q];
+                for (int q = 0; q < 3; ++q) s.frow[lr][q] += s.gY[0][e][q];
             }
         }
         __syncthreads();
@@ -506,11 +510,11 @@ int bwd_impl(const Model& m, const EdgeArgs& a, cudaStream_t st) {
     if (a.first) {
         MP_CUDA_TRY(cudaFuncSetAttribute(k_edge_bwd<F, LMAX, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_edge_bwd<F, LMAX, true><<<grid, F, sm, st>>>(a, w.W1, w.W2, w.W2T, w.W3, w.W3T);
+        k_edge_bwd<F, LMAX, true><<<grid, F, sm, st>>>(a, w.W1, w.W2T, w.W3T);
     } else {
         MP_CUDA_TRY(cudaFuncSetAttribute(k_edge_bwd<F, LMAX, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_edge_bwd<F, LMAX, false><<<grid, F, sm, st>>>(a, w.W1, w.W2, w.W2T, w.W3, w.W3T);
+        k_edge_bwd<F, LMAX, false><<<grid, F, sm, st>>>(a, w.W1, w.W2T, w.W3T);
     }
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;

@@ -104,17 +104,17 @@ __device__ __forceinline__ void sph_harm(const float u[3], float* Y) {
 }
 
 // v = sum_lm gY_lm dY_lm/du (gY indexed like Y, entry 0 unused).
-template <int LMAX>
-__device__ __forceinline__ void sph_grad(const float u[3], const float* gY, float v[3]) {
-    const float s3 = 1.7320508075688772f;
+template <int LMAX, class T = float>
+__device__ __forceinline__ void sph_grad(const T u[3], const T* gY, T v[3]) {
+    const T s3 = (T)1.7320508075688772;
     v[0] = s3 * gY[1];
     v[1] = s3 * gY[2];
     v[2] = s3 * gY[3];
     if (LMAX >= 2) {
-        const float s15 = 3.872983346207417f, s5 = 2.23606797749979f;
+        const T s15 = (T)3.872983346207417, s5 = (T)2.23606797749979;
         v[0] += s15 * (gY[4] * u[1] + gY[7] * u[2] + gY[8] * u[0]);
         v[1] += s15 * (gY[4] * u[0] + gY[5] * u[2] - gY[8] * u[1]);
-        v[2] += s15 * (gY[5] * u[1] + gY[7] * u[0]) + 3.f * s5 * gY[6] * u[2];
+        v[2] += s15 * (gY[5] * u[1] + gY[7] * u[0]) + (T)3 * s5 * gY[6] * u[2];
     }
 }
 
