@@ -1,0 +1,352 @@
+"""Benchmark: velocity-Verlet MD throughput (atom-steps/s) of the depth-pruned
+message-passing potential on one GB300 per rank.
+
+Default workload (N=1): 1,048,576-atom FCC Cu (64^3 cubic cells, a = 3.615 A),
+Maxwell velocities at 600 K, pruned K = 2 layers of the 6-layer model (F = 128,
+lmax = 2, r_c = 6 A), 8 z-slab partitions with a 12 A geometric halo processed
+one after another, dt = 1 fs.  A step is one full MD step: neighbour list,
+partitions, energy + forces through the hand-written adjoint, Verlet update.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision bf16|fp32] [--layers K] [--parts P] [--cells n]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (a 6x6x6-cell block of the same lattice and model) on the host cores.
+Under torchrun every rank simulates its own independent copy of the system
+(no data-path collective, weak scaling); value = all ranks' atom-steps / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MD atom-steps/s on 1 GB300 at 32k/1M atoms; force error vs FP64 oracle"
+UNIT = "atom-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["bf16", "fp32"])
+    ap.add_argument("--layers", type=int, default=2)
+    ap.add_argument("--parts", type=int, default=8)
+    ap.add_argument("--cells", type=int, default=64, help="FCC cells per axis")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    import synth
+    s = synth.cu_fcc_large(cells=(args.cells,) * 3, sigma=0.0, seed=4)
+    d = synth.model_cu(n_layers_full=6)
+    w = synth.make_weights(d, 4)
+    v = synth.maxwell(s.masses, 600.0, 4)
+    return s, d, w, v
+
+
+def config_dict(args, n_atoms):
+    return {"workload": "fcc-cu-%d-md-600K" % n_atoms, "atoms": n_atoms,
+            "layers_K": args.layers, "layers_full": 6, "F": 128, "lmax": 2, "r_cut_A": 6.0,
+            "partitions": args.parts, "halo_A": 6.0 * args.layers, "halo_mode": "geometric",
+            "dt_fs": 1.0, "precision": args.precision,
+            "l2": "inputs larger than L2 (per-partition features >> 129 MB)"}
+
+
+# -------------------------------------------------------------- clocks --
+
+class Clocks:
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self, dev_index=0):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(dev_index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- roofline --
+
+def edge_flops(kind: str, F: int, lmax: int, first: bool) -> float:
+    """Algorithmic FLOPs per directed edge (2 per multiply-add)."""
+    H, NB = 64, 8
+    n_paths = (1 + lmax) if first else (1 + 2 * lmax)
+    mlp = NB * H + H * H + H * n_paths * F                       # one MLP pass, MACs
+    if kind == "fwd":
+        msg = F * (1 + sum((1 + (2 * l + 1) * (1 if first else 2)) for l in range(1, lmax + 1)))
+        return 2.0 * (mlp + msg)
+    # adjoint: MLP value + tangent, dR . dE/dR, sender gradients, dE/dR, dE/dY
+    epi = F * (2 * n_paths + (0 if first else 1 + sum(2 * (2 * l + 1) for l in range(1, lmax + 1)))
+               + sum(4 * (2 * l + 1) for l in range(1, lmax + 1)) + 2)
+    return 2.0 * (2 * mlp + epi)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------- our arm --
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_2509_21694_gb300 import build
+    build.build()
+    from paper_2509_21694_gb300 import binding as mp
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s, d, w, v0 = workload(args)
+    n = len(s.pos)
+    prec = mp.MP_BF16 if args.precision == "bf16" else mp.MP_FP32
+    stream = torch.cuda.current_stream()
+    ctx = mp.mp_create(d, w)
+    mp.mp_set_stream(ctx, stream.cuda_stream)
+    pos = torch.tensor(s.pos, device=dev)
+    vel = torch.tensor(v0, device=dev)
+    frc = torch.zeros(n, 3, dtype=torch.float32, device=dev)
+    mass = torch.tensor(s.masses, device=dev)
+    sp = torch.tensor(s.species, device=dev)
+    md = dict(n_layers=args.layers, precision=prec, n_parts=args.parts, k_hops=args.layers,
+              halo_mode=mp.MP_HALO_GEOM)
+
+    # warm-up (also computes the initial forces)
+    mp.mp_md_step(ctx, pos, vel, frc, mass, sp, s.box, 1.0, args.warmup, **md)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = Clocks()
+    mp.mp_timing_enable(ctx, True)
+    launches0 = mp.mp_kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    ledger = mp.mp_md_step(ctx, pos, vel, frc, mass, sp, s.box, 1.0, args.steps,
+                           forces_valid=True, **md)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop(local)
+    launches = mp.mp_kernel_launches() - launches0
+    timing = mp.mp_timing_read(ctx)
+    mp.mp_timing_enable(ctx, False)
+    ms = t0.elapsed_time(t1)
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * n * args.steps / (ms_max * 1e-3)
+
+    # end-to-end through the C ABI from pinned host buffers: every step copies
+    # positions and velocities in, runs one MD step and reads back positions,
+    # velocities, forces and the energy ledger.
+    e2e = None
+    if not args.no_e2e:
+        h_pos = torch.tensor(pos.cpu().numpy()).pin_memory()
+        h_vel = torch.tensor(vel.cpu().numpy()).pin_memory()
+        h_frc = torch.empty(n, 3, dtype=torch.float32).pin_memory()
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            pos.copy_(h_pos, non_blocking=True)
+            vel.copy_(h_vel, non_blocking=True)
+            mp.mp_md_step(ctx, pos, vel, frc, mass, sp, s.box, 1.0, 1, forces_valid=True, **md)
+            h_pos.copy_(pos, non_blocking=True)
+            h_vel.copy_(vel, non_blocking=True)
+            h_frc.copy_(frc, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * n * args.steps / (ems * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": 2 * n * 3 * 8,
+               "d2h_bytes_per_step": 2 * n * 3 * 8 + n * 3 * 4 + 3 * 8}
+
+    # roofline of the dominant kernel class
+    peaks, peak_kind = load_peaks()
+    dom = max(("edge_fwd", "edge_bwd", "node_fwd", "node_bwd", "neighbors", "partition"),
+              key=lambda k: timing[k]["ms"])
+    roof = None
+    t = timing[dom]
+    if dom in ("edge_fwd", "edge_bwd") and t["launches"]:
+        kind = "fwd" if dom == "edge_fwd" else "bwd"
+        # layer 0 launches process the first-layer form, the rest the full form
+        per_layer = t["edges"] / t["launches"]
+        flops_first = edge_flops(kind, 128, 2, True)
+        flops_rest = edge_flops(kind, 128, 2, False)
+        flops = per_layer * (flops_first + (args.layers - 1) * flops_rest) / args.layers
+        dur = t["ms"] / t["launches"] * 1e-3
+        achieved = flops / dur / 1e12
+        if args.precision == "fp32":
+            mhz = clk.get("sm_mhz") or 2070.0
+            peak = 152 * 128 * 2 * mhz * 1e6 / 1e12      # FP32 FFMA lanes x 2 FLOP x clock
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "k_edge_" + kind,
+                    "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x median SM clock %.0f MHz" % mhz,
+                    "flops_per_launch": flops}
+        else:
+            peak = peaks.get("bf16_tflops_sustained", 1700.0)
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "k_edge_" + kind,
+                    "peak_note": "bf16_tflops_sustained of %s peaks" % peak_kind,
+                    "flops_per_launch": flops}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16+fp32" if args.precision == "bf16" else "fp32", "data": "synthetic",
+           "config": config_dict(args, n), "e2e": e2e, "gpu_launches": launches,
+           "roofline": roof, "clocks": clk,
+           "kernel_ms": {k: round(v["ms"], 3) for k, v in timing.items()},
+           "energy_drift_first_last_eV": float(ledger[-1, 2] - ledger[0, 2]),
+           "peaks": peak_kind}
+    mp.mp_destroy(ctx)
+    return out
+
+
+# ------------------------------------------------------ oracle (CPU) --
+
+def oracle_sample_step(args, cells=6):
+    """One FP64 oracle MD step on a cells^3 block of the same lattice/model."""
+    import numpy as np
+    import synth
+    from oracle import md as omd, model as om, neighbors as onb
+    s = synth.cu_fcc_large(cells=(cells,) * 3, sigma=0.0, seed=4)
+    d = synth.model_cu(n_layers_full=6)
+    w = synth.make_weights(d, 4)
+    v = synth.maxwell(s.masses, 600.0, 4)
+
+    def force(p):
+        E, _, F = om.energy_forces(p, s.species, s.box, onb.edges(p, s.box, d.r_cut), w, d,
+                                   args.layers)
+        return E, F
+    state = {"pos": s.pos, "vel": v, "F": force(s.pos)[1]}
+
+    def step():
+        p, vv, F, _ = omd.verlet(state["pos"], state["vel"], s.masses, s.box, force, 1.0, 1,
+                                 forces=state["F"])
+        state.update(pos=p, vel=vv, F=F)
+    return len(s.pos), step
+
+
+def cpu_baseline(args, cells=6, steps=1):
+    import torch
+    torch.set_num_threads(os.cpu_count() or 1)
+    n, step = oracle_sample_step(args, cells)
+    t = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = time.perf_counter() - t
+    return {"value": n * steps / dt, "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": "%d-atom FCC Cu block (%d^3 cells) of the same lattice and model, K=%d, "
+                      "%d MD step(s), FP64 torch CPU" % (n, cells, args.layers, steps)}
+
+
+def run_reference(args):
+    import torch
+    torch.set_num_threads(os.cpu_count() or 1)
+    n, step = oracle_sample_step(args)
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t
+    value = n * args.steps / dt
+    cb = {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+          "sample": "%d-atom FCC Cu block of the same lattice and model per step, K=%d, FP64 "
+                    "torch CPU" % (n, args.layers)}
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, 4 * args.cells ** 3),
+            "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, cells=6, steps=3)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -188,6 +188,28 @@ int mp_md_step(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces,
                const double box[3], double dt_fs, int n_steps, const mp_md_opts* opts,
                double* h_ledger);
 
+/* ---- diagnostics ---------------------------------------------------------
+ * Per-context CUDA-event timing of kernel classes, on the context stream.
+ * The paper has no counterpart; these calls let a caller measure the
+ * library's kernels inside its own timed region. */
+#define MP_TIMER_NEIGHBORS   0   /* wrap, bin, cell sort, CSR count + fill     */
+#define MP_TIMER_PARTITION   1   /* root/halo flags, compaction, local CSR     */
+#define MP_TIMER_EDGE_FWD    2   /* edge forward (basis, radial MLP, messages) */
+#define MP_TIMER_EDGE_BWD    3   /* edge adjoint (forces, sender gradients)    */
+#define MP_TIMER_NODE_FWD    4   /* node update                                 */
+#define MP_TIMER_NODE_BWD    5   /* node adjoint                                */
+#define MP_TIMER_COUNT       6
+/* enable != 0 starts recording and clears the accumulators; 0 stops. */
+int mp_timing_enable(mp_ctx* ctx, int enable);
+/* Synchronises the stream, then fills host arrays of MP_TIMER_COUNT
+ * entries: total milliseconds, launches, edges and atoms processed. */
+int mp_timing_read(mp_ctx* ctx, double* ms, int64_t* launches, int64_t* edges, int64_t* atoms);
+
+/* Diagnostics: number of CUDA kernels this library has launched in this
+ * process so far (host counter, no synchronisation).  The paper has no
+ * counterpart; it lets a caller attribute GPU work to the library. */
+int mp_kernel_launches(int64_t* count);
+
 const char* mp_strerror(int code);
 
 #ifdef __cplusplus

@@ -72,6 +72,9 @@ def _load():
         "mp_energy_forces": (I32, [P, P, P, P, P, I32, I32, I32, P, P, P]),
         "mp_md_step": (I32, [P, P, P, P, P, P, I64, ctypes.POINTER(D), D, I32,
                              ctypes.POINTER(mp_md_opts), P]),
+        "mp_kernel_launches": (I32, [ctypes.POINTER(I64)]),
+        "mp_timing_enable": (I32, [P, I32]),
+        "mp_timing_read": (I32, [P, P, P, P, P]),
         "mp_strerror": (ctypes.c_char_p, [I32]),
     }
     for name, (res, args) in sig.items():
@@ -242,6 +245,29 @@ def mp_md_step(ctx: int, pos, vel, forces, mass, species, box, dt: float, n_step
                            pos.shape[0], b, dt, n_steps, ctypes.byref(opts),
                            led.ctypes.data if ledger else None), "mp_md_step")
     return led[:n_steps]
+
+
+TIMERS = ("neighbors", "partition", "edge_fwd", "edge_bwd", "node_fwd", "node_bwd")
+
+
+def mp_timing_enable(ctx: int, enable: bool = True):
+    _check(_lib.mp_timing_enable(ctx, int(enable)), "mp_timing_enable")
+
+
+def mp_timing_read(ctx: int) -> dict:
+    n = len(TIMERS)
+    ms = np.zeros(n, np.float64)
+    la, ed, at = (np.zeros(n, np.int64) for _ in range(3))
+    _check(_lib.mp_timing_read(ctx, ms.ctypes.data, la.ctypes.data, ed.ctypes.data,
+                               at.ctypes.data), "mp_timing_read")
+    return {name: {"ms": float(ms[q]), "launches": int(la[q]), "edges": int(ed[q]),
+                   "atoms": int(at[q])} for q, name in enumerate(TIMERS)}
+
+
+def mp_kernel_launches() -> int:
+    n = ctypes.c_int64()
+    _check(_lib.mp_kernel_launches(ctypes.byref(n)), "mp_kernel_launches")
+    return n.value
 
 
 def mp_strerror(code: int) -> str:

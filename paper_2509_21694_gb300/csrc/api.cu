@@ -1,11 +1,56 @@
 // C ABI entry points: argument checks, context / weights / object lifetime.
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "kernels.h"
 
 namespace mp {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+static cudaEvent_t take_event(Timing& t) {
+    if (!t.pool.empty()) {
+        cudaEvent_t e = t.pool.back();
+        t.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+TimerScope::TimerScope(mp_ctx* c, int id, int64_t edges, int64_t atoms) : ctx(c) {
+    if (!ctx->timing.on) return;
+    TimerRec r{id, take_event(ctx->timing), take_event(ctx->timing), edges, atoms};
+    cudaEventRecord(r.a, ctx->stream);
+    idx = (int)ctx->timing.recs.size();
+    ctx->timing.recs.push_back(r);
+}
+
+TimerScope::~TimerScope() {
+    if (idx >= 0) cudaEventRecord(ctx->timing.recs[idx].b, ctx->stream);
+}
+
+static void timing_collect(mp_ctx* ctx) {
+    Timing& t = ctx->timing;
+    for (TimerRec& r : t.recs) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            t.ms[r.id] += ms;
+            t.launches[r.id] += 1;
+            t.edges[r.id] += r.edges;
+            t.atoms[r.id] += r.atoms;
+        }
+        t.pool.push_back(r.a);
+        t.pool.push_back(r.b);
+    }
+    t.recs.clear();
+}
+
 int export_graph(const Graph& g, cudaStream_t st, int32_t* recv, int32_t* send, int8_t* sh);
 int export_plan(const Plan& plan, const Graph& g, int p, cudaStream_t st, int32_t* gid,
                 uint8_t* root);
@@ -211,6 +256,8 @@ void mp_destroy(mp_ctx* ctx) {
                       &w.eatom, &w.esum, &w.fsum, &w.ebuf, &w.err, &w.tmp, &w.xw,
                       &w.perm_pos, &w.pscr, &w.red};
     for (DevBuf* b : bufs) b->release();
+    timing_collect(ctx);
+    for (cudaEvent_t e : ctx->timing.pool) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -311,6 +358,37 @@ int mp_md_step(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const
     if (!ctx || !box || !(dt_fs > 0)) return MP_ERR_ARG;
     return md_run(ctx, d_pos, d_vel, d_forces, d_mass, d_species, n, box, dt_fs, n_steps, opts,
                   h_ledger);
+}
+
+int mp_timing_enable(mp_ctx* ctx, int enable) {
+    if (!ctx) return MP_ERR_ARG;
+    timing_collect(ctx);
+    Timing& t = ctx->timing;
+    for (int q = 0; q < MP_TIMER_COUNT; ++q) {
+        t.ms[q] = 0;
+        t.launches[q] = t.edges[q] = t.atoms[q] = 0;
+    }
+    t.on = enable != 0;
+    return MP_OK;
+}
+
+int mp_timing_read(mp_ctx* ctx, double* ms, int64_t* launches, int64_t* edges, int64_t* atoms) {
+    if (!ctx) return MP_ERR_ARG;
+    timing_collect(ctx);
+    const Timing& t = ctx->timing;
+    for (int q = 0; q < MP_TIMER_COUNT; ++q) {
+        if (ms) ms[q] = t.ms[q];
+        if (launches) launches[q] = t.launches[q];
+        if (edges) edges[q] = t.edges[q];
+        if (atoms) atoms[q] = t.atoms[q];
+    }
+    return MP_OK;
+}
+
+int mp_kernel_launches(int64_t* count) {
+    if (!count) return MP_ERR_ARG;
+    *count = launch_count();
+    return MP_OK;
 }
 
 const char* mp_strerror(int code) {

@@ -96,7 +96,7 @@ struct Plan {
 
 // Views of one sub-system (whole graph or one partition) for the evaluator.
 struct SubSys {
-    int64_t n;
+    int64_t n, n_edges;
     const int64_t* row_ptr;
     const int32_t* col;
     const int8_t* shift;
@@ -111,8 +111,26 @@ struct Workspace {
 
 }  // namespace mp
 
+namespace mp {
+// CUDA-event timing of kernel classes (diagnostics).
+struct TimerRec {
+    int id;
+    cudaEvent_t a, b;
+    int64_t edges, atoms;
+};
+struct Timing {
+    bool on = false;
+    std::vector<TimerRec> recs;
+    std::vector<cudaEvent_t> pool;
+    double ms[MP_TIMER_COUNT] = {0};
+    int64_t launches[MP_TIMER_COUNT] = {0}, edges[MP_TIMER_COUNT] = {0},
+            atoms[MP_TIMER_COUNT] = {0};
+};
+}  // namespace mp
+
 struct mp_ctx {
     mp::Model model;
+    mp::Timing timing;
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 0;
@@ -151,5 +169,18 @@ int md_run(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const dou
            const mp_md_opts* o, double* h_ledger);
 
 inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
+
+// RAII scope recording start/stop events of one kernel class when timing
+// is enabled on the context.
+struct TimerScope {
+    mp_ctx* ctx;
+    int idx = -1;
+    TimerScope(mp_ctx* c, int id, int64_t edges, int64_t atoms);
+    ~TimerScope();
+};
+
+// Process-wide count of kernel launches issued by this library.
+void note_launch();
+int64_t launch_count();
 
 }  // namespace mp

@@ -497,6 +497,7 @@ int fwd_impl(const Model& m, const EdgeArgs& a, cudaStream_t st) {
         k_edge_fwd<F, LMAX, true><<<grid, F, 0, st>>>(a, w.W1, w.W2T, w.W3T);
     else
         k_edge_fwd<F, LMAX, false><<<grid, F, 0, st>>>(a, w.W1, w.W2T, w.W3T);
+    note_launch();
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
@@ -510,11 +511,11 @@ int bwd_impl(const Model& m, const EdgeArgs& a, cudaStream_t st) {
     if (a.first) {
         MP_CUDA_TRY(cudaFuncSetAttribute(k_edge_bwd<F, LMAX, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_edge_bwd<F, LMAX, true><<<grid, F, sm, st>>>(a, w.W1, w.W2T, w.W3T);
+        k_edge_bwd<F, LMAX, true><<<grid, F, sm, st>>>(a, w.W1, w.W2T, w.W3T); note_launch();
     } else {
         MP_CUDA_TRY(cudaFuncSetAttribute(k_edge_bwd<F, LMAX, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_edge_bwd<F, LMAX, false><<<grid, F, sm, st>>>(a, w.W1, w.W2T, w.W3T);
+        k_edge_bwd<F, LMAX, false><<<grid, F, sm, st>>>(a, w.W1, w.W2T, w.W3T); note_launch();
     }
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;

@@ -214,11 +214,12 @@ int reduce_sum(const double* v, int64_t n, double* out, DevBuf& tmp, cudaStream_
     const int64_t per = (int64_t)kRedThreads * kRedItems;
     const int64_t blocks = n > 0 ? (n + per - 1) / per : 1;
     MP_TRY(tmp.reserve(sizeof(double) * blocks));
-    if (n > 0)
+    if (n > 0) {
         k_sum_partial<<<(unsigned)blocks, kRedThreads, 0, st>>>(v, n, tmp.as<double>());
-    else
+        note_launch();
+    } else
         MP_CUDA_TRY(cudaMemsetAsync(tmp.as<double>(), 0, sizeof(double), st));
-    k_sum_final<<<1, kRedThreads, 0, st>>>(tmp.as<double>(), blocks, out);
+    k_sum_final<<<1, kRedThreads, 0, st>>>(tmp.as<double>(), blocks, out); note_launch();
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
@@ -252,11 +253,11 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
     const double* x = b.xs;
     const int32_t* sp = b.sp;
     if (ss.gid) {
-        k_gather_local<<<grid_for(n, 256), 256, 0, st>>>(ss.gid, n, b.xs, b.sp, b.xl, b.spl);
+        k_gather_local<<<grid_for(n, 256), 256, 0, st>>>(ss.gid, n, b.xs, b.sp, b.xl, b.spl); note_launch();
         x = b.xl;
         sp = b.spl;
     }
-    k_embed<<<grid_for(feat, 256), 256, 0, st>>>(sp, n, F, NLM, m.emb, b.H);
+    k_embed<<<grid_for(feat, 256), 256, 0, st>>>(sp, n, F, NLM, m.emb, b.H); note_launch();
     EdgeArgs ea{};
     ea.n = n;
     ea.row_ptr = ss.row_ptr;
@@ -273,29 +274,35 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         ea.first = t == 0;
         ea.Hin = b.H + t * feat;
         ea.Aout = b.A + t * feat;
-        if (precision == MP_BF16)
-            MP_TRY(launch_edge_fwd_bf16(m, ea, st, ctx->num_sms));
-        else
-            MP_TRY(launch_edge_fwd_f32(m, ea, st));
+        {
+            TimerScope ts(ctx, MP_TIMER_EDGE_FWD, ss.n_edges, n);
+            if (precision == MP_BF16)
+                MP_TRY(launch_edge_fwd_bf16(m, ea, st, ctx->num_sms));
+            else
+                MP_TRY(launch_edge_fwd_f32(m, ea, st));
+        }
         na.w = &m.layers[t];
         na.A = b.A + t * feat;
         na.Hin = b.H + t * feat;
         na.Hout = b.H + (t + 1) * feat;
         na.S = b.S + t * n * F;
         na.last = t == K - 1;
-        MP_TRY(launch_node_fwd_f32(m, na, st));
+        {
+            TimerScope ts(ctx, MP_TIMER_NODE_FWD, 0, n);
+            MP_TRY(launch_node_fwd_f32(m, na, st));
+        }
     }
     {
         const int wpb = 4;
         k_readout<<<grid_for(n, wpb), 32 * wpb, sizeof(float) * F * wpb, st>>>(
             n, F, NLM, b.H + (int64_t)K * feat, sp, m.w_out, m.e0, use_head ? m.head : nullptr,
-            ss.is_root, b.eloc, b.G[K & 1]);
+            ss.is_root, b.eloc, b.G[K & 1]); note_launch();
     }
     MP_CUDA_TRY(cudaMemsetAsync(b.floc, 0, sizeof(double) * 3 * n, st));
     if (m.d.rep_eps != 0.0) {
         const int wpb = 8;
         k_pair_term<<<grid_for(n, wpb), 32 * wpb, 0, st>>>(n, ss.row_ptr, ss.col, ss.shift, x, kc,
-                                                           ss.is_root, b.eloc, b.floc);
+                                                           ss.is_root, b.eloc, b.floc); note_launch();
     }
     for (int t = K - 1; t >= 0; --t) {
         float* Gout = b.G[(t + 1) & 1];
@@ -306,7 +313,10 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         na.Gout = Gout;
         na.Alpha = b.alpha;
         na.last = t == K - 1;
-        MP_TRY(launch_node_bwd_f32(m, na, st));
+        {
+            TimerScope ts(ctx, MP_TIMER_NODE_BWD, 0, n);
+            MP_TRY(launch_node_bwd_f32(m, na, st));
+        }
         ea.w = &m.layers[t];
         ea.first = t == 0;
         ea.Hin = b.H + t * feat;
@@ -314,13 +324,16 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         ea.Gout = Gout;
         ea.Gin = t == 0 ? nullptr : Gin;
         ea.frc = b.floc;
-        if (precision == MP_BF16)
-            MP_TRY(launch_edge_bwd_bf16(m, ea, st, ctx->num_sms));
-        else
-            MP_TRY(launch_edge_bwd_f32(m, ea, st));
+        {
+            TimerScope ts(ctx, MP_TIMER_EDGE_BWD, ss.n_edges, n);
+            if (precision == MP_BF16)
+                MP_TRY(launch_edge_bwd_bf16(m, ea, st, ctx->num_sms));
+            else
+                MP_TRY(launch_edge_bwd_f32(m, ea, st));
+        }
     }
     k_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, ss.gid, ss.is_root, b.eloc, b.floc, b.e_sorted,
-                                                b.f_sorted);
+                                                b.f_sorted); note_launch();
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
@@ -342,11 +355,11 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
 
     std::vector<SubSys> subs;
     if (!plan) {
-        subs.push_back(SubSys{n, g.row_ptr.as<int64_t>(), g.col.as<int32_t>(),
+        subs.push_back(SubSys{n, g.n_edges, g.row_ptr.as<int64_t>(), g.col.as<int32_t>(),
                               g.shift.as<int8_t>(), nullptr, nullptr});
     } else {
         for (const Part& P : plan->parts)
-            subs.push_back(SubSys{P.n_ext, P.row_ptr.as<int64_t>(), P.col.as<int32_t>(),
+            subs.push_back(SubSys{P.n_ext, P.n_edges, P.row_ptr.as<int64_t>(), P.col.as<int32_t>(),
                                   P.shift.as<int8_t>(), P.gid.as<int32_t>(),
                                   P.is_root.as<uint8_t>()});
     }
@@ -385,13 +398,13 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
     b.eloc = ws.eatom.as<double>();
 
     k_gather_pos<<<grid_for(n, 256), 256, 0, st>>>(d_pos, d_species, g.perm.as<int32_t>(), n,
-                                                   g.box[0], g.box[1], g.box[2], b.xs, b.sp);
+                                                   g.box[0], g.box[1], g.box[2], b.xs, b.sp); note_launch();
     MP_CUDA_TRY(cudaMemsetAsync(b.f_sorted, 0, sizeof(double) * 3 * n, st));
     MP_CUDA_TRY(cudaMemsetAsync(b.e_sorted, 0, sizeof(double) * n, st));
     const EdgeConst kc = make_edge_const(m.d, g.box);
     for (const SubSys& s : subs) MP_TRY(run_subsystem(ctx, s, b, kc, K, precision, use_head));
     k_finalize<<<grid_for(n, 256), 256, 0, st>>>(n, g.perm.as<int32_t>(), b.e_sorted, b.f_sorted,
-                                                 d_forces, d_e_atom);
+                                                 d_forces, d_e_atom); note_launch();
     MP_TRY(reduce_sum(b.e_sorted, n, d_energy, ws.red, st));
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;

@@ -82,14 +82,14 @@ int md_run(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const dou
     if (!o->forces_valid) rc = forces();
     for (int s = 0; s < n_steps && rc == MP_OK; ++s) {
         k_kick_drift<<<grid_for(n, 256), 256, 0, st>>>(n, d_pos, d_vel, d_forces, d_mass, dt,
-                                                       box[0], box[1], box[2]);
+                                                       box[0], box[1], box[2]); note_launch();
         rc = forces();
         if (rc) break;
         k_kick_ke<<<grid_for(n, 256), 256, 0, st>>>(n, d_vel, d_forces, d_mass, dt,
-                                                    ke.as<double>());
+                                                    ke.as<double>()); note_launch();
         rc = reduce_sum(ke.as<double>(), n, kes, red, st);
         if (rc) break;
-        k_ledger<<<1, 1, 0, st>>>(pe, kes, led.as<double>() + 3 * s);
+        k_ledger<<<1, 1, 0, st>>>(pe, kes, led.as<double>() + 3 * s); note_launch();
         if (o->check_every > 0 && (s + 1) % o->check_every == 0) {
             double e = 0;
             if (cudaMemcpyAsync(&e, pe, sizeof(double), cudaMemcpyDeviceToHost, st) ||

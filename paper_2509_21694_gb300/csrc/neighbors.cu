@@ -232,6 +232,7 @@ int build_graph(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3]
     int64_t ncell = (int64_t)b.nc[0] * b.nc[1] * b.nc[2];
 
     Workspace& ws = ctx->ws;
+    TimerScope ts(ctx, MP_TIMER_NEIGHBORS, 0, n);
     MP_TRY(g.perm.reserve(sizeof(int32_t) * n));
     MP_TRY(g.inv.reserve(sizeof(int32_t) * n));
     MP_TRY(g.xs.reserve(sizeof(double) * 3 * n + sizeof(float4) * n + 64));
@@ -253,18 +254,18 @@ int build_graph(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3]
 
     MP_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int32_t) * (2 * ncell + 2), st));
     MP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
-    k_wrap_bin<<<grid_for(n, 256), 256, 0, st>>>(d_pos, n, b, xw, cell, count);
+    k_wrap_bin<<<grid_for(n, 256), 256, 0, st>>>(d_pos, n, b, xw, cell, count); note_launch();
     MP_TRY(exclusive_scan_i32(count, g.cell_start.as<int32_t>(), ncell, ws.tmp, st));
     k_place<<<grid_for(n, 256), 256, 0, st>>>(cell, n, g.cell_start.as<int32_t>(), cursor,
-                                              g.perm.as<int32_t>());
+                                              g.perm.as<int32_t>()); note_launch();
     k_sort_cells<<<grid_for(ncell, 128), 128, 0, st>>>(g.cell_start.as<int32_t>(), (int)ncell,
-                                                       g.perm.as<int32_t>());
+                                                       g.perm.as<int32_t>()); note_launch();
     k_gather_sorted<<<grid_for(n, 256), 256, 0, st>>>(g.perm.as<int32_t>(), n, xw,
-                                                      g.inv.as<int32_t>(), xs, xsf);
+                                                      g.inv.as<int32_t>(), xs, xsf); note_launch();
     int warps_per_block = 8;
     int nb = grid_for(n, warps_per_block);
     k_neighbors<false><<<nb, 32 * warps_per_block, 0, st>>>(
-        xsf, xs, n, b, g.cell_start.as<int32_t>(), deg, nullptr, nullptr, nullptr, err);
+        xsf, xs, n, b, g.cell_start.as<int32_t>(), deg, nullptr, nullptr, nullptr, err); note_launch();
     MP_TRY(exclusive_scan_i64(deg, g.row_ptr.as<int64_t>(), n, ws.tmp, st));
     int64_t ne = 0;
     MP_CUDA_TRY(cudaMemcpyAsync(&ne, g.row_ptr.as<int64_t>() + n, sizeof(int64_t),
@@ -278,7 +279,7 @@ int build_graph(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3]
     MP_TRY(g.shift.reserve(ne + 16));
     k_neighbors<true><<<nb, 32 * warps_per_block, 0, st>>>(
         xsf, xs, n, b, g.cell_start.as<int32_t>(), nullptr, g.row_ptr.as<int64_t>(),
-        g.col.as<int32_t>(), g.shift.as<int8_t>(), err);
+        g.col.as<int32_t>(), g.shift.as<int8_t>(), err); note_launch();
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
@@ -287,7 +288,7 @@ int export_graph(const Graph& g, cudaStream_t st, int32_t* recv, int32_t* send, 
     int wpb = 8;
     k_export<<<grid_for(g.n, wpb), 32 * wpb, 0, st>>>(g.row_ptr.as<int64_t>(),
                                                       g.col.as<int32_t>(), g.shift.as<int8_t>(),
-                                                      g.perm.as<int32_t>(), g.n, recv, send, sh);
+                                                      g.perm.as<int32_t>(), g.n, recv, send, sh); note_launch();
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

@@ -172,6 +172,7 @@ int node_fwd_impl(const NodeArgs& a, cudaStream_t st) {
         k_node_fwd<F, LMAX, true><<<grid, F, 0, st>>>(a, w.W0T, w.UT[0], U2T, w.b, w.VT[0], V2T);
     else
         k_node_fwd<F, LMAX, false><<<grid, F, 0, st>>>(a, w.W0T, w.UT[0], U2T, w.b, w.VT[0], V2T);
+    note_launch();
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
@@ -187,6 +188,7 @@ int node_bwd_impl(const NodeArgs& a, cudaStream_t st) {
         k_node_bwd<F, LMAX, true><<<grid, F, 0, st>>>(a, w.W0, w.U[0], U2, w.V[0], V2);
     else
         k_node_bwd<F, LMAX, false><<<grid, F, 0, st>>>(a, w.W0, w.U[0], U2, w.V[0], V2);
+    note_launch();
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

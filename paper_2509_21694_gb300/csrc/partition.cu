@@ -125,6 +125,7 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
     plan.n = n;
     plan.parts.resize(n_parts);
     Workspace& ws = ctx->ws;
+    TimerScope ts(ctx, MP_TIMER_PARTITION, 0, n);
     // scratch: flag[n], flag2[n], pre[n+1], g2l[n], root[n] bytes
     DevBuf& scratch = ws.pscr;
     MP_TRY(scratch.reserve(sizeof(int32_t) * (4 * n + 2) + n + 64));
@@ -144,13 +145,13 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
         Part& P = plan.parts[p];
         int32_t* cur = flag;
         if (mode == MP_HALO_GEOM) {
-            k_flags_geom<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, width, flag, root);
+            k_flags_geom<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, width, flag, root); note_launch();
         } else {
-            k_flags_root<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, flag, root);
+            k_flags_root<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, flag, root); note_launch();
             int32_t* other = flag2;
             for (int h = 0; h < k_hops; ++h) {
                 k_bfs_hop<<<grid_for(n, 256), 256, 0, st>>>(g.row_ptr.as<int64_t>(),
-                                                            g.col.as<int32_t>(), n, cur, other);
+                                                            g.col.as<int32_t>(), n, cur, other); note_launch();
                 int32_t* t = cur;
                 cur = other;
                 other = t;
@@ -166,10 +167,10 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
         if ((rc = P.is_root.reserve(P.n_ext + 16))) break;
         if ((rc = P.row_ptr.reserve(sizeof(int64_t) * (P.n_ext + 1)))) break;
         k_compact<<<grid_for(n, 256), 256, 0, st>>>(cur, pre, root, n, P.gid.as<int32_t>(),
-                                                    P.is_root.as<uint8_t>(), g2l);
+                                                    P.is_root.as<uint8_t>(), g2l); note_launch();
         int32_t* ldeg = cur == flag ? flag2 : flag;   // free flag buffer
         k_local_deg<<<grid_for(P.n_ext, 256), 256, 0, st>>>(
-            g.row_ptr.as<int64_t>(), g.col.as<int32_t>(), P.gid.as<int32_t>(), g2l, P.n_ext, ldeg);
+            g.row_ptr.as<int64_t>(), g.col.as<int32_t>(), P.gid.as<int32_t>(), g2l, P.n_ext, ldeg); note_launch();
         rc = exclusive_scan_i64(ldeg, P.row_ptr.as<int64_t>(), P.n_ext, ws.tmp, st);
         if (rc) break;
         int64_t ne = 0;
@@ -183,9 +184,9 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
         k_local_fill<<<grid_for(P.n_ext, 256), 256, 0, st>>>(
             g.row_ptr.as<int64_t>(), g.col.as<int32_t>(), g.shift.as<int8_t>(),
             P.gid.as<int32_t>(), g2l, P.n_ext, P.row_ptr.as<int64_t>(), P.col.as<int32_t>(),
-            P.shift.as<int8_t>());
+            P.shift.as<int8_t>()); note_launch();
         // root count: roots are flagged in `root` (uint8) -> count with a scan of flags
-        k_flags_root<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, ldeg, root);
+        k_flags_root<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, ldeg, root); note_launch();
         rc = exclusive_scan_i32(ldeg, pre, n, ws.tmp, st);
         if (rc) break;
         if (cudaMemcpyAsync(&nroot, pre + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st) ||
@@ -204,7 +205,7 @@ int export_plan(const Plan& plan, const Graph& g, int p, cudaStream_t st, int32_
     const Part& P = plan.parts[p];
     k_plan_export<<<grid_for(P.n_ext, 256), 256, 0, st>>>(P.gid.as<int32_t>(),
                                                           P.is_root.as<uint8_t>(),
-                                                          g.perm.as<int32_t>(), P.n_ext, gid, root);
+                                                          g.perm.as<int32_t>(), P.n_ext, gid, root); note_launch();
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

@@ -100,9 +100,9 @@ int scan_impl(const int32_t* in, Out* out, int64_t n, DevBuf& tmp, cudaStream_t 
     int64_t tiles = (n + kTile - 1) / kTile;
     MP_TRY(tmp.reserve(sizeof(Out) * (size_t)tiles));
     Out* sums = tmp.as<Out>();
-    k_tile_sums<Out><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
-    k_scan_small<Out><<<1, kScanThreads, 0, s>>>(sums, tiles);
-    k_tile_scan<Out><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums, out);
+    k_tile_sums<Out><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums); note_launch();
+    k_scan_small<Out><<<1, kScanThreads, 0, s>>>(sums, tiles); note_launch();
+    k_tile_scan<Out><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums, out); note_launch();
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
