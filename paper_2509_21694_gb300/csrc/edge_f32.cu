@@ -211,70 +211,87 @@ __global__ void __launch_bounds__(F) k_edge_fwd(EdgeArgs a, const float* __restr
 
 // ---------------------------------------------------------------- adjoint --
 
+constexpr int CB = 8;    // edges per chunk in the adjoint
+
 template <int F, int LMAX>
 struct BwdSmem {
     static constexpr int NLM = (LMAX + 1) * (LMAX + 1);
-    static constexpr int P = F * (1 + 2 * LMAX);
-    static constexpr int NW = F / 32;
-    float eps[CE][kNB];
-    float deps[CE][kNB];
-    float Y[CE][NLM];
-    float u[CE][4];          // unit vector, r
-    float a1[kH][CE], da1[kH][CE], a2[kH][CE], da2[kH][CE];
-    float gR[P][CE + 1];
-    double gY[NW][CE][NLM];
-    double gr[NW][CE];
+    static constexpr int NQ = NLM;           // q = 0: dE/dr partial, 1..: dE/dY_lm partials
+    float eps[CB][kNB];
+    float deps[CB][kNB];
+    float Y[CB][NLM];
+    float u[CB][4];          // unit vector, r
+    float a1[kH][CB], da1[kH][CB], a2[kH][CB], da2[kH][CB];
+    float part[CB][NQ][F + 1];
+    double red[CB][NQ];
     double frow[RPB][3];
-    int row[CE], col[CE];
+    int row[CB], col[CB];
     int64_t rp[RPB + 1];
 };
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+// R (value) and dR/dr (tangent) of the radial MLP's last layer for CB edges,
+// one pass over W3.
+template <int F, int LMAX, bool FIRST>
+__device__ __forceinline__ void radial_out2(const float* __restrict__ W3T,
+                                            const float (*s_a2)[CB], const float (*s_da2)[CB],
+                                            int c, float R[][CB], float dR[][CB]) {
+    using PP = Paths<LMAX, FIRST>;
+    constexpr int P = F * (1 + 2 * LMAX);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// a2 = silu(W2 a1) and its r-derivative da2 = silu'(z2) W2 da1 (forward mode).
-template <int F>
-__device__ __forceinline__ void hidden2_tangent(const float* __restrict__ W2T,
-                                                const float (*s_a1)[CE], const float (*s_da1)[CE],
-                                                float (*s_a2)[CE], float (*s_da2)[CE], int c) {
-    constexpr int EG = CE * kH / F;
-    const int kk = c % kH, e0 = (c / kH) * EG;
-    float z[EG], dz[EG];
+    for (int q = 0; q < PP::NP; ++q)
 #pragma unroll
-    for (int q = 0; q < EG; ++q) z[q] = dz[q] = 0.f;
-#pragma unroll 4
-    for (int jj = 0; jj < kH; ++jj) {
-        const float wv = __ldg(&W2T[jj * kH + kk]);
+        for (int e = 0; e < CB; ++e) R[q][e] = dR[q][e] = 0.f;
+#pragma unroll 2
+    for (int kk = 0; kk < kH; ++kk) {
+        float wv[PP::NP];
 #pragma unroll
-        for (int q = 0; q < EG; ++q) {
-            z[q] = fmaf(wv, s_a1[jj][e0 + q], z[q]);
-            dz[q] = fmaf(wv, s_da1[jj][e0 + q], dz[q]);
+        for (int q = 0; q < PP::NP; ++q) wv[q] = __ldg(&W3T[kk * P + PP::block(q) * F + c]);
+        float av[CB], dv[CB];
+#pragma unroll
+        for (int e4 = 0; e4 < CB / 4; ++e4) {
+            const float4 v = reinterpret_cast<const float4*>(s_a2[kk])[e4];
+            const float4 w = reinterpret_cast<const float4*>(s_da2[kk])[e4];
+            av[4 * e4] = v.x; av[4 * e4 + 1] = v.y; av[4 * e4 + 2] = v.z; av[4 * e4 + 3] = v.w;
+            dv[4 * e4] = w.x; dv[4 * e4 + 1] = w.y; dv[4 * e4 + 2] = w.z; dv[4 * e4 + 3] = w.w;
         }
-    }
 #pragma unroll
-    for (int q = 0; q < EG; ++q) {
-        s_a2[kk][e0 + q] = silu(z[q]);
-        s_da2[kk][e0 + q] = silu_grad(z[q]) * dz[q];
+        for (int q = 0; q < PP::NP; ++q)
+#pragma unroll
+            for (int e = 0; e < CB; ++e) {
+                R[q][e] = fmaf(wv[q], av[e], R[q][e]);
+                dR[q][e] = fmaf(wv[q], dv[e], dR[q][e]);
+            }
     }
 }
 
-// Adjoint of one layer.  dE/dr of an edge pair is obtained as
-// sum_q dE/dR_q * dR_q/dr with dR/dr propagated forward through the radial
-// MLP (it depends on the geometry only); the sums over channels run in FP64.
+// Compensated (Kahan) sum of n floats with stride 1, result in double.
+__device__ __forceinline__ double kahan_sum(const float* v, int n) {
+    float s = 0.f, comp = 0.f;
+    for (int q = 0; q < n; ++q) {
+        const float y = v[q] - comp;
+        const float t = s + y;
+        comp = (t - s) - y;
+        s = t;
+    }
+    return (double)s - (double)comp;
+}
+
+// Adjoint of one layer.  dE/dr of an edge pair is sum_q dE/dR_q dR_q/dr with
+// dR/dr propagated forward through the radial MLP (it depends on the
+// geometry only).  Per-edge sums over channels (dE/dr, dE/dY) go through
+// shared memory and a compensated FP32 sum per (edge, quantity).
 template <int F, int LMAX, bool FIRST>
 __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restrict__ W1,
                                                 const float* __restrict__ W2T,
                                                 const float* __restrict__ W3T) {
     using PP = Paths<LMAX, FIRST>;
     using SM = BwdSmem<F, LMAX>;
-    constexpr int NLM = SM::NLM;
+    constexpr int NLM = SM::NLM, NQ = SM::NQ;
+    constexpr int EG = CB * kH / F;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SM& s = *reinterpret_cast<SM*>(smem_raw);
 
-    const int c = threadIdx.x, lane = c & 31, warp = c >> 5;
+    const int c = threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.x * RPB;
     const int nrows = (int)min((int64_t)RPB, a.n - r0);
     if (c <= nrows) s.rp[c] = a.row_ptr[r0 + c];
@@ -294,8 +311,8 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
             a.Gin[base + q * F] = a.Gout[base + q * F] + (with_acc ? gacc[q] : 0.f);
     };
 
-    for (int64_t cb = e_beg; cb < e_end; cb += CE) {
-        if (c < CE) {
+    for (int64_t cb = e_beg; cb < e_end; cb += CB) {
+        if (c < CB) {
             const int64_t e = cb + c;
             float eps[kNB], deps[kNB], Y[NLM], u4[4] = {0.f, 0.f, 0.f, 1.f};
             if (e < e_end) {
@@ -332,8 +349,8 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
             for (int q = 0; q < 4; ++q) s.u[c][q] = u4[q];
         }
         __syncthreads();
-        for (int o = c; o < kH * CE; o += F) {
-            const int kk = o / CE, e = o % CE;
+        for (int o = c; o < kH * CB; o += F) {
+            const int kk = o / CB, e = o % CB;
             float z = 0.f, dz = 0.f;
 #pragma unroll
             for (int b = 0; b < kNB; ++b) {
@@ -345,15 +362,38 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
             s.da1[kk][e] = silu_grad(z) * dz;
         }
         __syncthreads();
-        hidden2_tangent<F>(W2T, s.a1, s.da1, s.a2, s.da2, c);
+        {
+            const int kk = c % kH, e0 = (c / kH) * EG;
+            float z[EG], dz[EG];
+#pragma unroll
+            for (int q = 0; q < EG; ++q) z[q] = dz[q] = 0.f;
+#pragma unroll 4
+            for (int jj = 0; jj < kH; ++jj) {
+                const float wv = __ldg(&W2T[jj * kH + kk]);
+#pragma unroll
+                for (int q = 0; q < EG; ++q) {
+                    z[q] = fmaf(wv, s.a1[jj][e0 + q], z[q]);
+                    dz[q] = fmaf(wv, s.da1[jj][e0 + q], dz[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < EG; ++q) {
+                s.a2[kk][e0 + q] = silu(z[q]);
+                s.da2[kk][e0 + q] = silu_grad(z[q]) * dz[q];
+            }
+        }
         __syncthreads();
-        float R[PP::NP][CE];
-        radial_out<F, LMAX, FIRST>(W3T, s.a2, c, R);
+        float R[PP::NP][CB], dR[PP::NP][CB];
+        radial_out2<F, LMAX, FIRST>(W3T, s.a2, s.da2, c, R, dR);
 
 #pragma unroll
-        for (int e = 0; e < CE; ++e) {
+        for (int e = 0; e < CB; ++e) {
             const int lr = s.row[e];
-            if (lr < 0) break;
+            if (lr < 0) {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) s.part[e][q][c] = 0.f;
+                continue;
+            }
             if (lr != cur) {
                 if (cur >= 0) {
                     flush(cur, true);
@@ -401,20 +441,19 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
                 }
                 gacc[0] += g0;
             }
-            // (b) dE/dR summed over both directions; (c) dE/dY partial sums
-            s.gR[c][e] = ak[0] * hj[0] + aj[0] * hk[0];
-            float gy[NLM];
+            // (b) dE/dR of both directions contracted with dR/dr; (c) dE/dY
+            float gr = (ak[0] * hj[0] + aj[0] * hk[0]) * dR[0][e];
             {
                 float g1a = 0.f, g1b = 0.f;
 #pragma unroll
                 for (int m = 0; m < 3; ++m) {
                     const float t = ak[1 + m] * hj[0] - aj[1 + m] * hk[0];
                     g1a = fmaf(Y[1 + m], t, g1a);
-                    gy[1 + m] = R[PP::sla(1)][e] * t;
+                    s.part[e][1 + m][c] = R[PP::sla(1)][e] * t;
                     if (!FIRST) g1b += ak[1 + m] * hj[1 + m] + aj[1 + m] * hk[1 + m];
                 }
-                s.gR[F + c][e] = g1a;
-                if (!FIRST) s.gR[2 * F + c][e] = g1b;
+                gr = fmaf(g1a, dR[PP::sla(1)][e], gr);
+                if (!FIRST) gr = fmaf(g1b, dR[PP::slb(1)][e], gr);
             }
             if (LMAX >= 2) {
                 float g2a = 0.f, g2b = 0.f;
@@ -422,59 +461,39 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
                 for (int m = 0; m < 5; ++m) {
                     const float t = ak[4 + m] * hj[0] + aj[4 + m] * hk[0];
                     g2a = fmaf(Y[4 + m], t, g2a);
-                    gy[4 + m] = R[PP::sla(2)][e] * t;
+                    s.part[e][4 + m][c] = R[PP::sla(2)][e] * t;
                     if (!FIRST) g2b += ak[4 + m] * hj[4 + m] + aj[4 + m] * hk[4 + m];
                 }
-                s.gR[3 * F + c][e] = g2a;
-                if (!FIRST) s.gR[4 * F + c][e] = g2b;
+                gr = fmaf(g2a, dR[PP::sla(2)][e], gr);
+                if (!FIRST) gr = fmaf(g2b, dR[PP::slb(2)][e], gr);
             }
-#pragma unroll
-            for (int q = 1; q < NLM; ++q) {
-                const double v = warp_sum_d((double)gy[q]);
-                if (lane == 0) s.gY[warp][e][q] = v;
-            }
-        }
-        // dR/dr for this thread's channel (same registers as R), contracted
-        // with dE/dR; the channel sum runs in FP64.
-        radial_out<F, LMAX, FIRST>(W3T, s.da2, c, R);
-#pragma unroll
-        for (int e = 0; e < CE; ++e) {
-            float part = 0.f;
-#pragma unroll
-            for (int q = 0; q < PP::NP; ++q) part = fmaf(s.gR[PP::block(q) * F + c][e], R[q][e], part);
-            const double v = warp_sum_d((double)part);
-            if (lane == 0) s.gr[warp][e] = v;
+            s.part[e][0][c] = gr;
         }
         __syncthreads();
-        if (c < CE && s.row[c] >= 0) {
+        for (int t = c; t < CB * NQ; t += F) s.red[t / NQ][t % NQ] = kahan_sum(s.part[t / NQ][t % NQ], F);
+        __syncthreads();
+        if (c < CB && s.row[c] >= 0) {
             const int e = c;
-            double gr = 0.0, gY[NLM];
-#pragma unroll
-            for (int w = 0; w < SM::NW; ++w) gr += s.gr[w][e];
+            const double gr = s.red[e][0];
+            double gY[NLM];
             gY[0] = 0.0;
 #pragma unroll
-            for (int q = 1; q < NLM; ++q) {
-                double v = 0.0;
-#pragma unroll
-                for (int w = 0; w < SM::NW; ++w) v += s.gY[w][e][q];
-                gY[q] = v;
-            }
+            for (int q = 1; q < NLM; ++q) gY[q] = s.red[e][q];
             const double u[3] = {s.u[e][0], s.u[e][1], s.u[e][2]};
             const double ir = 1.0 / (double)s.u[e][3];
             double v[3];
             sph_grad<LMAX, double>(u, gY, v);
             const double vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
-            // row sums in a fixed order by one thread per chunk
 #pragma unroll
-            for (int q = 0; q < 3; ++q) s.gY[0][e][q] = gr * u[q] + (v[q] - vu * u[q]) * ir;
+            for (int q = 0; q < 3; ++q) s.red[e][q] = gr * u[q] + (v[q] - vu * u[q]) * ir;
         }
         __syncthreads();
         if (c == 0) {
-            for (int e = 0; e < CE; ++e) {
+            for (int e = 0; e < CB; ++e) {
                 const int lr = s.row[e];
                 if (lr < 0) break;
 #pragma unroll
-                for (int q = 0; q < 3; ++q) s.frow[lr][q] += s.gY[0][e][q];
+                for (int q = 0; q < 3; ++q) s.frow[lr][q] += s.red[e][q];
             }
         }
         __syncthreads();
