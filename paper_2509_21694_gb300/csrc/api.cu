@@ -93,7 +93,8 @@ static int upload_model(Model& m, const double* w) {
     auto takeh = [&](size_t k) { size_t o = nh; nh += (k + 63) / 64 * 64; return o; };
     size_t o_emb = takef((size_t)S * F), o_e0 = takef(S), o_wout = takef(F),
            o_head = takef((size_t)Hh * F + 2 * Hh + 1);
-    struct LO { size_t W1, W2, W2T, W3, W3T, W0, W0T, U[2], UT[2], b, V[2], VT[2]; size_t W2b, W3b, W3Tb, W2Tb; };
+    struct LO { size_t W1, W2, W2T, W3, W3T, W0, W0T, U[2], UT[2], b, V[2], VT[2]; size_t W2b, W3b, W3Tb, W2Tb, W2sw, W3sw; };
+    const bool tc_shape = (F == 128 && lm == 2 && H == 64);
     std::vector<LO> lo(L);
     for (int t = 0; t < L; ++t) {
         lo[t].W1 = takef((size_t)H * NB);
@@ -114,6 +115,8 @@ static int upload_model(Model& m, const double* w) {
         lo[t].W3b = takeh((size_t)P * H);
         lo[t].W3Tb = takeh((size_t)P * H);
         lo[t].W2Tb = takeh((size_t)H * H);
+        lo[t].W2sw = tc_shape ? takeh((size_t)128 * H) : 0;
+        lo[t].W3sw = tc_shape ? takeh((size_t)P * H) : 0;
     }
     std::vector<float> hf(nf, 0.f);
     std::vector<__nv_bfloat16> hh(nh > 0 ? nh : 1);
@@ -149,6 +152,21 @@ static int upload_model(Model& m, const double* w) {
             hh[lo[t].W3b + q] = __float2bfloat16_rn(hf[lo[t].W3 + q]);
             hh[lo[t].W3Tb + q] = __float2bfloat16_rn(hf[lo[t].W3T + q]);
         }
+        if (tc_shape) {
+            // swizzled images: element (row, k) at byte sw128_off(row, k) of its tile
+            auto put = [&](size_t base, int row, int k, float v) {
+                const int byte = row * 128 + ((((k >> 3) ^ (row & 7)) & 7) << 4) + (k & 7) * 2;
+                hh[base + byte / 2] = __float2bfloat16_rn(v);
+            };
+            for (size_t q = 0; q < (size_t)128 * H; ++q) hh[lo[t].W2sw + q] = __float2bfloat16_rn(0.f);
+            for (int r = 0; r < H; ++r)
+                for (int k = 0; k < H; ++k) put(lo[t].W2sw, r, k, hf[lo[t].W2 + (size_t)r * H + k]);
+            for (int tile = 0; tile < P / 128; ++tile)
+                for (int r = 0; r < 128; ++r)
+                    for (int k = 0; k < H; ++k)
+                        put(lo[t].W3sw + (size_t)tile * 128 * H, r, k,
+                            hf[lo[t].W3 + (size_t)(tile * 128 + r) * H + k]);
+        }
     }
     const size_t fbytes = nf * sizeof(float), hbytes = hh.size() * sizeof(__nv_bfloat16);
     MP_TRY(m.store.reserve(fbytes + hbytes + 256));
@@ -182,6 +200,8 @@ static int upload_model(Model& m, const double* w) {
         q.W3b = hbase + lo[t].W3b;
         q.W3Tb = hbase + lo[t].W3Tb;
         q.W2Tb = hbase + lo[t].W2Tb;
+        q.W2sw = tc_shape ? hbase + lo[t].W2sw : nullptr;
+        q.W3sw = tc_shape ? hbase + lo[t].W3sw : nullptr;
     }
     return MP_OK;
 }

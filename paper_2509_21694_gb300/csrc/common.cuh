@@ -57,6 +57,11 @@ struct LayerW {
     __nv_bfloat16* W3b;    // [P][H]   K-major
     __nv_bfloat16* W3Tb;   // [H][P]   (backward operand, K = P)
     __nv_bfloat16* W2Tb;   // [H][H]   (in, out)
+    // Tensor-core operand images, already laid out as K-major tiles with the
+    // 128-byte swizzle (rows of 64 BF16): W2 padded to 128 rows with zeros,
+    // W3 as (1 + 2 lmax) tiles of 128 rows (one per radial path).
+    __nv_bfloat16* W2sw;
+    __nv_bfloat16* W3sw;
 };
 
 struct Model {

@@ -266,6 +266,7 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
     ea.x = x;
     ea.k = kc;
     ea.seed = ss.is_root;
+    ea.err = ctx->ws.err.as<int>();
     NodeArgs na{};
     na.n = n;
     na.inv_navg = kc.inv_navg;
@@ -380,6 +381,8 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
     MP_TRY(ws.G1.reserve(sizeof(float) * feat));
     MP_TRY(ws.floc.reserve(sizeof(double) * 3 * nmax));
     MP_TRY(ws.eatom.reserve(sizeof(double) * nmax));
+    MP_TRY(ws.err.reserve(64));
+    MP_CUDA_TRY(cudaMemsetAsync(ws.err.as<int>(), 0, sizeof(int), st));
 
     EvalBufs b;
     b.xs = ws.xw.as<double>();
@@ -407,6 +410,13 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
                                                  d_forces, d_e_atom); note_launch();
     MP_TRY(reduce_sum(b.e_sorted, n, d_energy, ws.red, st));
     MP_CUDA_TRY(cudaGetLastError());
+    if (precision == MP_BF16 && K > 0) {
+        // tensor-core kernels report bounded-wait timeouts in the error word
+        int herr = 0;
+        MP_CUDA_TRY(cudaMemcpyAsync(&herr, ws.err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+        MP_CUDA_TRY(cudaStreamSynchronize(st));
+        if (herr) return MP_ERR_TIMEOUT;
+    }
     return MP_OK;
 }
 

@@ -23,6 +23,7 @@ struct EdgeArgs {
     const uint8_t* seed;      // adjoint: root flags (null = all 1)
     double* frc;              // adjoint: [n][3] forces, accumulated
     bool first;               // layer 0: input l >= 1 features are zero
+    int* err;                 // device error word (bit 2: bounded wait timed out)
 };
 
 int launch_edge_fwd_f32(const Model& m, const EdgeArgs& a, cudaStream_t st);
