@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(F) k_edge_fwd(EdgeArgs a, const float* __restr
                 for (int q = 0; q < NLM; ++q) acc[q] = 0.f;
             }
             const float* hj = a.Hin + ((int64_t)s_col[e] * NLM) * F + c;
-            const float h0 = hj[0];
+            const float h0 = __ldg(hj);
             acc[0] = fmaf(R[0][e], h0, acc[0]);
             const float t1 = R[PP::sla(1)][e] * h0;
 #pragma unroll

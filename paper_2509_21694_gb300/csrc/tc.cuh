@@ -96,15 +96,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity: gives up after
-// max_polls polls (with a short sleep between), returning false.
+// Bounded wait for the phase with the given parity: spins on try_wait and
+// gives up (returning false) once max_cycles SM clock cycles have passed.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity,
-                                          uint32_t max_polls = 1u << 22) {
-    for (uint32_t q = 0; q < max_polls; ++q) {
-        if (mbar_try_wait(mbar, parity)) return true;
-        __nanosleep(32);
+                                          long long max_cycles = 2000000000LL) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        for (int q = 0; q < 64; ++q)
+            if (mbar_try_wait(mbar, parity)) return true;
+        if (clock64() - t0 > max_cycles) return false;
     }
-    return false;
 }
 
 // ---- tensor memory loads (32 lanes x 32-bit, N consecutive columns) -----------
@@ -119,6 +121,20 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
     for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+__device__ __forceinline__ void tmem_ld1(uint32_t taddr, float& v) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    v = __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float v[2]) {
+    uint32_t r0, r1;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1)
+                 : "r"(taddr));
+    v[0] = __uint_as_float(r0);
+    v[1] = __uint_as_float(r1);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     uint32_t r[16];
     asm volatile(
@@ -130,6 +146,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
         : "r"(taddr));
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+    tmem_ld16(taddr, v);
+    tmem_ld16(taddr + 16, v + 16);
 }
 
 __device__ __forceinline__ void tmem_wait_ld() {
