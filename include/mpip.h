@@ -52,6 +52,7 @@ extern "C" {
 #define MP_ERR_NOMEM          -7  /* device allocation failed                   */
 #define MP_ERR_UNSUPPORTED    -8  /* model shape not compiled in (F, lmax, ...) */
 #define MP_ERR_TIMEOUT        -9  /* a bounded wait ran out                     */
+#define MP_ERR_TOO_LARGE     -10  /* size beyond a fixed, documented maximum    */
 
 /* ---- precision and partition modes --------------------------------------- */
 #define MP_FP32  0   /* every contraction in FP32 on CUDA cores               */
@@ -209,6 +210,37 @@ int mp_timing_read(mp_ctx* ctx, double* ms, int64_t* launches, int64_t* edges, i
  * process so far (host counter, no synchronisation).  The paper has no
  * counterpart; it lets a caller attribute GPU work to the library. */
 int mp_kernel_launches(int64_t* count);
+
+/* ---- energy sum without device allocation ---------------------------------
+ * Some callers cannot allocate device memory at the moment they need a
+ * result: an MD engine that reserves all of its GPU memory in a pool at
+ * start-up and forbids cudaMalloc/cudaFree during a run (they synchronise
+ * the device and fragment the pool), or code running where an allocation
+ * failure cannot be handled.  This call sums per-atom energies exactly as
+ * mp_energy_forces does for its d_energy output (FP64, fixed block tree,
+ * same order) but keeps its block partial sums in a fixed array compiled
+ * into the library instead of allocating scratch.  The paper has no
+ * counterpart; it is a service for such callers.
+ *   d_e_atom   [n] double, device (e.g. the d_e_atom output of
+ *              mp_energy_forces).
+ *   d_energy   [1] double, device, written.
+ *   cuda_stream  stream to run on (NULL = legacy default stream).
+ * Limits and behaviour:
+ *   - n <= MP_NOALLOC_MAX_ATOMS, else MP_ERR_TOO_LARGE and nothing runs.
+ *   - Allocates nothing (no cudaMalloc, cudaFree or allocating library
+ *     routine).  The fixed array (MP_NOALLOC_MAX_PARTIALS doubles, 128 KB)
+ *     exists on every GPU that loads the library until the process exits.
+ *   - The first call on a device looks up that array's device address
+ *     (with the device current) and caches it; make that first call before
+ *     any stream capture.
+ *   - All calls on a GPU share that GPU's array, which keeps the last call's
+ *     partial sums: calls that overlap on one GPU (for example on two
+ *     streams) race and must be ordered by the caller.  Every partial is
+ *     rewritten before it is read, so nothing needs clearing between calls.
+ * Errors: MP_ERR_ARG (null pointer, n < 0), MP_ERR_TOO_LARGE, MP_ERR_CUDA. */
+#define MP_NOALLOC_MAX_PARTIALS 16384
+#define MP_NOALLOC_MAX_ATOMS    (MP_NOALLOC_MAX_PARTIALS * 2048LL)
+int mp_energy_sum_noalloc(const double* d_e_atom, int64_t n, double* d_energy, void* cuda_stream);
 
 const char* mp_strerror(int code);
 

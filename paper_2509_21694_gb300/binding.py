@@ -23,7 +23,8 @@ MP_FP32, MP_BF16 = 0, 1
 MP_HALO_GEOM, MP_HALO_BFS = 0, 1
 ERRORS = {-1: "MP_ERR_ARG", -2: "MP_ERR_BOX_TOO_SMALL", -3: "MP_ERR_OVERLAP",
           -4: "MP_ERR_CAPACITY", -5: "MP_ERR_CUDA", -6: "MP_ERR_NOT_FINITE",
-          -7: "MP_ERR_NOMEM", -8: "MP_ERR_UNSUPPORTED", -9: "MP_ERR_TIMEOUT"}
+          -7: "MP_ERR_NOMEM", -8: "MP_ERR_UNSUPPORTED", -9: "MP_ERR_TIMEOUT",
+          -10: "MP_ERR_TOO_LARGE"}
 
 
 class MPError(RuntimeError):
@@ -75,6 +76,7 @@ def _load():
         "mp_kernel_launches": (I32, [ctypes.POINTER(I64)]),
         "mp_timing_enable": (I32, [P, I32]),
         "mp_timing_read": (I32, [P, P, P, P, P]),
+        "mp_energy_sum_noalloc": (I32, [P, I64, P, P]),
         "mp_strerror": (ctypes.c_char_p, [I32]),
     }
     for name, (res, args) in sig.items():
@@ -268,6 +270,16 @@ def mp_kernel_launches() -> int:
     n = ctypes.c_int64()
     _check(_lib.mp_kernel_launches(ctypes.byref(n)), "mp_kernel_launches")
     return n.value
+
+
+MP_NOALLOC_MAX_ATOMS = 16384 * 2048
+
+
+def mp_energy_sum_noalloc(e_atom: torch.Tensor, energy: torch.Tensor, n: int | None = None):
+    """Sum of per-atom energies into energy[0] without any device allocation."""
+    n = e_atom.shape[0] if n is None else n
+    _check(_lib.mp_energy_sum_noalloc(_ptr(e_atom), n, _ptr(energy), _stream()),
+           "mp_energy_sum_noalloc")
 
 
 def mp_strerror(code: int) -> str:

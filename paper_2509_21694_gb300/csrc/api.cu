@@ -423,6 +423,7 @@ const char* mp_strerror(int code) {
         case MP_ERR_NOMEM: return "device allocation failed";
         case MP_ERR_UNSUPPORTED: return "model shape not compiled in";
         case MP_ERR_TIMEOUT: return "bounded wait timed out";
+        case MP_ERR_TOO_LARGE: return "size exceeds the fixed maximum of this call";
         default: return "unknown error";
     }
 }
