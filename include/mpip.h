@@ -189,6 +189,31 @@ int mp_md_step(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces,
                const double box[3], double dt_fs, int n_steps, const mp_md_opts* opts,
                double* h_ledger);
 
+/* ---- correction head: training -------------------------------------------
+ * The learned part: a per-atom head E_i^head = w2 . silu(W1 h0_i^(K) + b1)
+ * + b2 on the pruned model's final scalar features, trained on energies and
+ * forces of a reference model (the full-depth network) with the backbone
+ * frozen.  Loss of one snapshot of N atoms:
+ *   L = ((E - E_ref) / N)^2 + lambda / (3N) sum_k |F_k - F_ref,k|^2,
+ * E and F the student's (backbone + head).  The gradient's force term needs
+ * the tangent of h0^(K) along F - F_ref, computed by a forward-mode pass of
+ * the backbone on the GPU.  Head parameters live in the context (packed as
+ * in mp_create: W1[Hh][F], b1[Hh], w2[Hh], b2), count Hh F + 2 Hh + 1. */
+int mp_head_count(const mp_ctx* ctx, int64_t* n_out);
+/* Loss (and gradient, when d_grad != NULL) for one snapshot, whole graph.
+ *   d_e_ref  [1] double device; d_f_ref [n][3] float device (caller order).
+ *   d_loss   [1] double device, written; d_grad [mp_head_count] double
+ *            device, written.   n_layers = K >= 1. */
+int mp_head_loss_grad(mp_ctx* ctx, const double* d_pos, const int32_t* d_species,
+                      const mp_graph* g, int n_layers, int precision, const double* d_e_ref,
+                      const float* d_f_ref, double lambda_f, double* d_loss, double* d_grad);
+/* One Adam step on the context's head parameters with gradient d_grad;
+ * step = 1 resets the moment estimates. */
+int mp_head_adam_step(mp_ctx* ctx, const double* d_grad, double lr, double beta1, double beta2,
+                      double eps, int64_t step);
+/* Host copy of the current head parameters (synchronises). */
+int mp_head_get(mp_ctx* ctx, double* h_params, int64_t n);
+
 /* ---- diagnostics ---------------------------------------------------------
  * Per-context CUDA-event timing of kernel classes, on the context stream.
  * The paper has no counterpart; these calls let a caller measure the

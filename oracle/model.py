@@ -77,6 +77,8 @@ def sph_harm(u, lmax: int):
 
 
 def _t(a):
+    if isinstance(a, torch.Tensor):
+        return a
     return torch.as_tensor(np.asarray(a), dtype=_T)
 
 

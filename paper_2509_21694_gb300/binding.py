@@ -77,6 +77,10 @@ def _load():
         "mp_timing_enable": (I32, [P, I32]),
         "mp_timing_read": (I32, [P, P, P, P, P]),
         "mp_energy_sum_noalloc": (I32, [P, I64, P, P]),
+        "mp_head_count": (I32, [P, ctypes.POINTER(I64)]),
+        "mp_head_loss_grad": (I32, [P, P, P, P, I32, I32, P, P, D, P, P]),
+        "mp_head_adam_step": (I32, [P, P, D, D, D, D, I64]),
+        "mp_head_get": (I32, [P, P, I64]),
         "mp_strerror": (ctypes.c_char_p, [I32]),
     }
     for name, (res, args) in sig.items():
@@ -270,6 +274,36 @@ def mp_kernel_launches() -> int:
     n = ctypes.c_int64()
     _check(_lib.mp_kernel_launches(ctypes.byref(n)), "mp_kernel_launches")
     return n.value
+
+
+def mp_head_count(ctx: int) -> int:
+    n = ctypes.c_int64()
+    _check(_lib.mp_head_count(ctx, ctypes.byref(n)), "mp_head_count")
+    return n.value
+
+
+def mp_head_loss_grad(ctx: int, pos, species, g: int, n_layers: int, e_ref, f_ref,
+                      lambda_f: float = 1.0, precision: int = MP_FP32, grad: bool = True):
+    """(loss [1] double, grad [n_head] double or None) on the device."""
+    loss = torch.empty(1, dtype=torch.float64, device=pos.device)
+    gr = (torch.empty(mp_head_count(ctx), dtype=torch.float64, device=pos.device)
+          if grad else None)
+    _check(_lib.mp_head_loss_grad(ctx, _ptr(pos), _ptr(species), g, n_layers, precision,
+                                  _ptr(e_ref), _ptr(f_ref), float(lambda_f), _ptr(loss),
+                                  _ptr(gr)), "mp_head_loss_grad")
+    return loss, gr
+
+
+def mp_head_adam_step(ctx: int, grad, lr: float, step: int, beta1: float = 0.9,
+                      beta2: float = 0.999, eps: float = 1e-8):
+    _check(_lib.mp_head_adam_step(ctx, _ptr(grad), lr, beta1, beta2, eps, step),
+           "mp_head_adam_step")
+
+
+def mp_head_get(ctx: int) -> np.ndarray:
+    out = np.zeros(mp_head_count(ctx), dtype=np.float64)
+    _check(_lib.mp_head_get(ctx, out.ctypes.data, out.size), "mp_head_get")
+    return out
 
 
 MP_NOALLOC_MAX_ATOMS = 16384 * 2048

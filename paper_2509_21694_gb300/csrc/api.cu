@@ -274,7 +274,7 @@ void mp_destroy(mp_ctx* ctx) {
     Workspace& w = ctx->ws;
     DevBuf* bufs[] = {&w.xl, &w.sp, &w.H, &w.A, &w.S, &w.G0, &w.G1, &w.alpha, &w.floc,
                       &w.eatom, &w.esum, &w.fsum, &w.ebuf, &w.err, &w.tmp, &w.xw,
-                      &w.perm_pos, &w.pscr, &w.red};
+                      &w.perm_pos, &w.pscr, &w.red, &w.headbuf, &w.adam};
     for (DevBuf* b : bufs) b->release();
     timing_collect(ctx);
     for (cudaEvent_t e : ctx->timing.pool) cudaEventDestroy(e);
@@ -378,6 +378,36 @@ int mp_md_step(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const
     if (!ctx || !box || !(dt_fs > 0)) return MP_ERR_ARG;
     return md_run(ctx, d_pos, d_vel, d_forces, d_mass, d_species, n, box, dt_fs, n_steps, opts,
                   h_ledger);
+}
+
+int mp_head_count(const mp_ctx* ctx, int64_t* n_out) {
+    if (!ctx || !n_out) return MP_ERR_ARG;
+    *n_out = head_param_count(ctx->model);
+    return MP_OK;
+}
+
+int mp_head_loss_grad(mp_ctx* ctx, const double* d_pos, const int32_t* d_species,
+                      const mp_graph* g, int n_layers, int precision, const double* d_e_ref,
+                      const float* d_f_ref, double lambda_f, double* d_loss, double* d_grad) {
+    if (!ctx || !g || !(lambda_f >= 0)) return MP_ERR_ARG;
+    return head_loss_grad(ctx, d_pos, d_species, g->g, n_layers, precision, d_e_ref, d_f_ref,
+                          lambda_f, d_loss, d_grad);
+}
+
+int mp_head_adam_step(mp_ctx* ctx, const double* d_grad, double lr, double beta1, double beta2,
+                      double eps, int64_t step) {
+    if (!ctx) return MP_ERR_ARG;
+    return head_adam(ctx, d_grad, lr, beta1, beta2, eps, step);
+}
+
+int mp_head_get(mp_ctx* ctx, double* h_params, int64_t n) {
+    if (!ctx || !h_params || n != head_param_count(ctx->model)) return MP_ERR_ARG;
+    std::vector<float> h(n);
+    MP_CUDA_TRY(cudaMemcpyAsync(h.data(), ctx->model.head, sizeof(float) * n,
+                                cudaMemcpyDeviceToHost, ctx->stream));
+    MP_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    for (int64_t q = 0; q < n; ++q) h_params[q] = h[q];
+    return MP_OK;
 }
 
 int mp_timing_enable(mp_ctx* ctx, int enable) {

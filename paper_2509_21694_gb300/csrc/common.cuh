@@ -111,7 +111,7 @@ struct SubSys {
 
 struct Workspace {
     DevBuf xl, sp, H, A, S, G0, G1, alpha, floc, eatom, esum, fsum, ebuf,
-        err, tmp, xw, perm_pos, pscr, red;
+        err, tmp, xw, perm_pos, pscr, red, headbuf, adam;
 };
 
 }  // namespace mp
@@ -165,6 +165,13 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
 int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,
              const Plan* plan, int n_layers, int precision, int use_head, double* d_energy,
              float* d_forces, double* d_e_atom);
+// head.cu
+int64_t head_param_count(const Model& m);
+int head_loss_grad(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,
+                   int K, int precision, const double* d_e_ref, const float* d_f_ref,
+                   double lambda, double* d_loss, double* d_grad);
+int head_adam(mp_ctx* ctx, const double* d_grad, double lr, double beta1, double beta2,
+              double eps, int64_t step);
 // scan.cu
 int exclusive_scan_i64(const int32_t* in, int64_t* out, int64_t n, DevBuf& tmp, cudaStream_t s);
 int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, DevBuf& tmp, cudaStream_t s);

@@ -48,4 +48,26 @@ struct NodeArgs {
 int launch_node_fwd_f32(const Model& m, const NodeArgs& a, cudaStream_t st);
 int launch_node_bwd_f32(const Model& m, const NodeArgs& a, cudaStream_t st);
 
+// Tangent (forward-mode) pass of one layer along a displacement field v.
+struct TangentArgs {
+    int64_t n;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const int8_t* shift;
+    const double* x;          // [n][3] wrapped positions
+    const float* v;           // [n][3] displacement field
+    EdgeConst k;
+    const LayerW* w;
+    const float* Hin;         // [n][NLM][F] layer input values
+    const float* dHin;        // [n][NLM][F] layer input tangents (ignored at layer 0)
+    float* dAout;             // edge kernel output: message tangents (/N_avg)
+    const float* A;           // node kernel: layer messages
+    const float* dA;          // node kernel: message tangents
+    const float* S;           // node kernel: pre-activations
+    float* dHout;             // node kernel output: layer output tangents
+    bool first, last;
+};
+int launch_edge_tangent_f32(const Model& m, const TangentArgs& a, cudaStream_t st);
+int launch_node_tangent_f32(const Model& m, const TangentArgs& a, cudaStream_t st);
+
 }  // namespace mp
