@@ -119,3 +119,30 @@ def partitioned_energy_forces(pos, species, box, edges, w, desc, n_layers, parts
         Ei[gid[r]] = Eip[r]
         F[gid] += Fp
     return E, Ei, F
+
+
+def local_energy_force(pos, species, box, w, desc, n_layers, k, use_head=False):
+    """E_k and F_k of one atom of an arbitrarily large periodic system, exact.
+
+    Only atoms within K hops of k have energies that depend on r_k, and each
+    hop is shorter than r_c, so roots = {i : |r_i - r_k| < K r_c} (minimum
+    image).  Their energies are exact on the extended set
+    {j : |r_j - r_k| < 2 K r_c} with the edges among it (the partition
+    argument above applied to one spherical root set), and
+    F_k = -d(sum_roots E_i)/d r_k.
+    """
+    from .neighbors import brute_force_edges
+    x = wrap(np.asarray(pos, dtype=np.float64), box)
+    d = x - x[k]
+    d -= box * np.round(d / box)
+    r = np.sqrt((d * d).sum(1))
+    K = n_layers
+    roots = r < K * desc.r_cut
+    ext = r < 2 * K * desc.r_cut + 1e-6
+    gid = np.nonzero(ext)[0]
+    sub = x[gid]
+    e = brute_force_edges(sub, box, desc.r_cut)
+    _, Ei, F = energy_forces(sub, species[gid], box, e, w, desc, n_layers,
+                             seed_mask=roots[gid].astype(np.float64), use_head=use_head)
+    kl = int(np.searchsorted(gid, k))
+    return float(Ei[kl]), F[kl]

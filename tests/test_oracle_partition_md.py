@@ -110,3 +110,15 @@ def test_drift_slope_units():
     led[:, 2] = 5.0 + 2e-3 * np.arange(1, 11)     # +2 meV per step total
     # 100 atoms, dt = 1 fs: 2e-3 eV / 100 atoms per fs = 0.02 meV/atom/fs = 20 meV/atom/ps
     assert abs(omd.drift_mev_per_atom_ps(led, 100, 1.0) - 20.0) < 1e-9
+
+
+def test_local_cluster_force_equals_full_evaluation():
+    # One atom's E and F from its local cluster equal the whole-system result.
+    s = synth.alloy_fcc(cells=(8, 8, 8), sigma=0.1, seed=2)
+    d = synth.ModelDesc(n_species=2, F=16, lmax=2, n_layers_full=2, r_cut=3.5, n_avg=20.0)
+    w = synth.make_weights(d, 3)
+    E, Ei, F = om.energy_forces(s.pos, s.species, s.box, nb.edges(s.pos, s.box, d.r_cut), w, d, 2)
+    for k in (5, 777, 2047):
+        Ek, Fk = op.local_energy_force(s.pos, s.species, s.box, w, d, 2, k)
+        assert abs(Ek - Ei[k]) <= 1e-12 * abs(Ei[k])
+        assert np.abs(Fk - F[k]).max() <= 1e-12 * max(1.0, np.abs(F[k]).max())
