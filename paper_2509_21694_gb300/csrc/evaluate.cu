@@ -144,7 +144,7 @@ __global__ void k_pair_term(int64_t n, const int64_t* __restrict__ row_ptr,
         for (int q = 0; q < 3; ++q) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
     }
     if (lane == 0) {
-        Ei[i] += (double)ei;
+        if (si != 0.f) Ei[i] += (double)ei;   // energies of non-roots are never read
 #pragma unroll
         for (int q = 0; q < 3; ++q) frc[3 * i + q] += (double)f[q];
     }
@@ -242,6 +242,22 @@ struct EvalBufs {
     double* eloc;
 };
 
+// Rows a pass must cover: atoms within `hops` hops of a root (a prefix of
+// the local numbering for partitions, all atoms otherwise), and their edges.
+struct Prefix {
+    const SubSys& ss;
+    int64_t rows(int hops) const {
+        if (ss.n_le.empty()) return ss.n;
+        const int kp = (int)ss.n_le.size() - 1;
+        return ss.n_le[hops < 0 ? 0 : (hops > kp ? kp : hops)];
+    }
+    int64_t edges(int hops) const {
+        if (ss.e_le.empty()) return ss.n_edges;
+        const int kp = (int)ss.e_le.size() - 1;
+        return ss.e_le[hops < 0 ? 0 : (hops > kp ? kp : hops)];
+    }
+};
+
 int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeConst& kc, int K,
                   int precision, int use_head) {
     const Model& m = ctx->model;
@@ -250,16 +266,19 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
     const int64_t n = ss.n;
     if (n == 0) return MP_OK;
     const int64_t feat = n * NLM * F;
+    const int64_t row_f = (int64_t)NLM * F;   // floats per atom in a feature array
+    const Prefix pre{ss};
     const double* x = b.xs;
     const int32_t* sp = b.sp;
     if (ss.gid) {
-        k_gather_local<<<grid_for(n, 256), 256, 0, st>>>(ss.gid, n, b.xs, b.sp, b.xl, b.spl); note_launch();
+        k_gather_local<<<grid_for(n, 256), 256, 0, st>>>(ss.gid, n, b.xs, b.sp, b.xl, b.spl);
+        note_launch();
         x = b.xl;
         sp = b.spl;
     }
-    k_embed<<<grid_for(feat, 256), 256, 0, st>>>(sp, n, F, NLM, m.emb, b.H); note_launch();
+    k_embed<<<grid_for(feat, 256), 256, 0, st>>>(sp, n, F, NLM, m.emb, b.H);
+    note_launch();
     EdgeArgs ea{};
-    ea.n = n;
     ea.row_ptr = ss.row_ptr;
     ea.col = ss.col;
     ea.shift = ss.shift;
@@ -268,20 +287,25 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
     ea.seed = ss.is_root;
     ea.err = ctx->ws.err.as<int>();
     NodeArgs na{};
-    na.n = n;
     na.inv_navg = kc.inv_navg;
+    // Forward: layer t only needs outputs within K-1-t hops of a root; the
+    // rest of the next feature array is set to zero (never multiplied by a
+    // nonzero coefficient, but kept finite).
     for (int t = 0; t < K; ++t) {
+        const int64_t rows = pre.rows(K - 1 - t);
+        ea.n = rows;
         ea.w = &m.layers[t];
         ea.first = t == 0;
         ea.Hin = b.H + t * feat;
         ea.Aout = b.A + t * feat;
         {
-            TimerScope ts(ctx, MP_TIMER_EDGE_FWD, ss.n_edges, n);
+            TimerScope ts(ctx, MP_TIMER_EDGE_FWD, pre.edges(K - 1 - t), rows);
             if (precision == MP_BF16)
                 MP_TRY(launch_edge_fwd_bf16(m, ea, st, ctx->num_sms));
             else
                 MP_TRY(launch_edge_fwd_f32(m, ea, st));
         }
+        na.n = rows;
         na.w = &m.layers[t];
         na.A = b.A + t * feat;
         na.Hin = b.H + t * feat;
@@ -289,25 +313,42 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         na.S = b.S + t * n * F;
         na.last = t == K - 1;
         {
-            TimerScope ts(ctx, MP_TIMER_NODE_FWD, 0, n);
+            TimerScope ts(ctx, MP_TIMER_NODE_FWD, 0, rows);
             MP_TRY(launch_node_fwd_f32(m, na, st));
         }
+        if (rows < n)
+            MP_CUDA_TRY(cudaMemsetAsync(b.H + (t + 1) * feat + rows * row_f, 0,
+                                        sizeof(float) * (n - rows) * row_f, st));
     }
+    // Readout on roots; adjoint seeds of every other atom are zero.
+    const int64_t n_roots = pre.rows(0);
     {
         const int wpb = 4;
-        k_readout<<<grid_for(n, wpb), 32 * wpb, sizeof(float) * F * wpb, st>>>(
-            n, F, NLM, b.H + (int64_t)K * feat, sp, m.w_out, m.e0, use_head ? m.head : nullptr,
-            ss.is_root, b.eloc, b.G[K & 1]); note_launch();
+        k_readout<<<grid_for(n_roots, wpb), 32 * wpb, sizeof(float) * F * wpb, st>>>(
+            n_roots, F, NLM, b.H + (int64_t)K * feat, sp, m.w_out, m.e0,
+            use_head ? m.head : nullptr, ss.is_root, b.eloc, b.G[K & 1]);
+        note_launch();
+        if (n_roots < n)
+            MP_CUDA_TRY(cudaMemsetAsync(b.G[K & 1] + n_roots * row_f, 0,
+                                        sizeof(float) * (n - n_roots) * row_f, st));
     }
     MP_CUDA_TRY(cudaMemsetAsync(b.floc, 0, sizeof(double) * 3 * n, st));
     if (m.d.rep_eps != 0.0) {
         const int wpb = 8;
-        k_pair_term<<<grid_for(n, wpb), 32 * wpb, 0, st>>>(n, ss.row_ptr, ss.col, ss.shift, x, kc,
-                                                           ss.is_root, b.eloc, b.floc); note_launch();
+        // atoms beyond one hop of a root have no root neighbour: zero force
+        const int64_t n_pair = pre.rows(1);
+        k_pair_term<<<grid_for(n_pair, wpb), 32 * wpb, 0, st>>>(n_pair, ss.row_ptr, ss.col, ss.shift, x, kc,
+                                                           ss.is_root, b.eloc, b.floc);
+        note_launch();
     }
+    // Adjoint: alpha of layer t is nonzero only within K-1-t hops (node pass
+    // there, zero beyond); the edge pass covers rows within K-t hops, and the
+    // rows beyond it keep dE/dh = the layer output's (zero there).
     for (int t = K - 1; t >= 0; --t) {
         float* Gout = b.G[(t + 1) & 1];
         float* Gin = b.G[t & 1];
+        const int64_t nrows = pre.rows(K - 1 - t);
+        na.n = nrows;
         na.w = &m.layers[t];
         na.A = b.A + t * feat;
         na.S = b.S + t * n * F;
@@ -315,9 +356,14 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         na.Alpha = b.alpha;
         na.last = t == K - 1;
         {
-            TimerScope ts(ctx, MP_TIMER_NODE_BWD, 0, n);
+            TimerScope ts(ctx, MP_TIMER_NODE_BWD, 0, nrows);
             MP_TRY(launch_node_bwd_f32(m, na, st));
         }
+        if (nrows < n)
+            MP_CUDA_TRY(cudaMemsetAsync(b.alpha + nrows * row_f, 0,
+                                        sizeof(float) * (n - nrows) * row_f, st));
+        const int64_t erows = pre.rows(K - t);
+        ea.n = erows;
         ea.w = &m.layers[t];
         ea.first = t == 0;
         ea.Hin = b.H + t * feat;
@@ -326,15 +372,20 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         ea.Gin = t == 0 ? nullptr : Gin;
         ea.frc = b.floc;
         {
-            TimerScope ts(ctx, MP_TIMER_EDGE_BWD, ss.n_edges, n);
+            TimerScope ts(ctx, MP_TIMER_EDGE_BWD, pre.edges(K - t), erows);
             if (precision == MP_BF16)
                 MP_TRY(launch_edge_bwd_bf16(m, ea, st, ctx->num_sms));
             else
                 MP_TRY(launch_edge_bwd_f32(m, ea, st));
         }
+        if (t > 0 && erows < n)
+            MP_CUDA_TRY(cudaMemcpyAsync(Gin + erows * row_f, Gout + erows * row_f,
+                                        sizeof(float) * (n - erows) * row_f,
+                                        cudaMemcpyDeviceToDevice, st));
     }
     k_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, ss.gid, ss.is_root, b.eloc, b.floc, b.e_sorted,
-                                                b.f_sorted); note_launch();
+                                                b.f_sorted);
+    note_launch();
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
@@ -357,12 +408,12 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
     std::vector<SubSys> subs;
     if (!plan) {
         subs.push_back(SubSys{n, g.n_edges, g.row_ptr.as<int64_t>(), g.col.as<int32_t>(),
-                              g.shift.as<int8_t>(), nullptr, nullptr});
+                              g.shift.as<int8_t>(), nullptr, nullptr, {}, {}});
     } else {
         for (const Part& P : plan->parts)
             subs.push_back(SubSys{P.n_ext, P.n_edges, P.row_ptr.as<int64_t>(), P.col.as<int32_t>(),
                                   P.shift.as<int8_t>(), P.gid.as<int32_t>(),
-                                  P.is_root.as<uint8_t>()});
+                                  P.is_root.as<uint8_t>(), P.n_le, P.e_le});
     }
     int64_t nmax = 0;
     for (const SubSys& s : subs) nmax = s.n > nmax ? s.n : nmax;

@@ -7,6 +7,9 @@
 // halo of width K r_c (MP_HALO_GEOM, a superset: each hop is shorter than
 // r_c).  The extended set keeps ascending cell order, so each local row holds
 // the global row's edges in the same order, filtered to senders in the set.
+// Local atoms are ordered by hop class (roots, then atoms within r_c of the
+// slab or one hop of a root, ...), each class in cell order, so the rows a
+// layer needs form a prefix of the local numbering.
 #include "common.cuh"
 
 namespace mp {
@@ -17,59 +20,6 @@ __device__ __forceinline__ int root_bin(double z, double L, int P) {
     double f = __ddiv_rn(z, L);
     int b = (int)floor(__dmul_rn(f, (double)P));
     return b < P - 1 ? b : P - 1;
-}
-
-__global__ void k_flags_geom(const double* __restrict__ xs, int64_t n, double Lz, int P, int p,
-                             double width, int32_t* __restrict__ flag, uint8_t* __restrict__ root) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    double z = xs[3 * s + 2];
-    bool r = root_bin(z, Lz, P) == p;
-    double lo = __ddiv_rn(__dmul_rn(Lz, (double)p), (double)P);
-    double hi = __ddiv_rn(__dmul_rn(Lz, (double)(p + 1)), (double)P);
-    bool below = z < lo;
-    double d_lo = below ? __dsub_rn(lo, z) : __dsub_rn(__dadd_rn(lo, Lz), z);
-    double d_hi = below ? __dsub_rn(__dadd_rn(z, Lz), hi) : __dsub_rn(z, hi);
-    double dist = d_lo < d_hi ? d_lo : d_hi;
-    flag[s] = (r || dist < width) ? 1 : 0;
-    root[s] = r ? 1 : 0;
-}
-
-__global__ void k_flags_root(const double* __restrict__ xs, int64_t n, double Lz, int P, int p,
-                             int32_t* __restrict__ flag, uint8_t* __restrict__ root) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    bool r = root_bin(xs[3 * s + 2], Lz, P) == p;
-    flag[s] = r ? 1 : 0;
-    root[s] = r ? 1 : 0;
-}
-
-// One BFS hop over the symmetric edge set (pull form).
-__global__ void k_bfs_hop(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                          int64_t n, const int32_t* __restrict__ cur, int32_t* __restrict__ nxt) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    int v = cur[s];
-    if (!v) {
-        for (int64_t e = row_ptr[s]; e < row_ptr[s + 1]; ++e)
-            if (cur[col[e]]) { v = 1; break; }
-    }
-    nxt[s] = v;
-}
-
-__global__ void k_compact(const int32_t* __restrict__ flag, const int32_t* __restrict__ pre,
-                          const uint8_t* __restrict__ root, int64_t n, int32_t* __restrict__ gid,
-                          uint8_t* __restrict__ lroot, int32_t* __restrict__ g2l) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    if (flag[s]) {
-        int l = pre[s];
-        gid[l] = (int32_t)s;
-        lroot[l] = root[s];
-        g2l[s] = l;
-    } else {
-        g2l[s] = -1;
-    }
 }
 
 __global__ void k_local_deg(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -102,6 +52,77 @@ __global__ void k_local_fill(const int64_t* __restrict__ row_ptr, const int32_t*
     }
 }
 
+// Hop class of every atom for partition p: 0 = root, m = 1..K = halo atom
+// whose z-distance to the slab is below m r_c + s_m and not below
+// (m-1) r_c + s_{m-1}, K + 1 = outside the extended set.  s_K = 1e-6 (the
+// halo width rule) and s_m = 1e-6 m / K below it: a neighbour of a class-m
+// atom is closer than (m+1) r_c + s_m, so it has class <= m + 1 with a
+// margin of 1e-6 / K over rounding, and any atom h hops from a root has
+// class <= h.
+__global__ void k_class_geom(const double* __restrict__ xs, int64_t n, double Lz, int P, int p,
+                             double rc, int K, int32_t* __restrict__ cls) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double z = xs[3 * s + 2];
+    if (root_bin(z, Lz, P) == p) {
+        cls[s] = 0;
+        return;
+    }
+    const double lo = __ddiv_rn(__dmul_rn(Lz, (double)p), (double)P);
+    const double hi = __ddiv_rn(__dmul_rn(Lz, (double)(p + 1)), (double)P);
+    const bool below = z < lo;
+    const double d_lo = below ? __dsub_rn(lo, z) : __dsub_rn(__dadd_rn(lo, Lz), z);
+    const double d_hi = below ? __dsub_rn(__dadd_rn(z, Lz), hi) : __dsub_rn(z, hi);
+    const double dist = d_lo < d_hi ? d_lo : d_hi;
+    int c = K + 1;
+    for (int m = 1; m <= K; ++m) {
+        const double slack = m == K ? 1e-6 : __ddiv_rn(__dmul_rn(1e-6, (double)m), (double)K);
+        if (dist < __dadd_rn(__dmul_rn((double)m, rc), slack)) { c = m; break; }
+    }
+    cls[s] = c;
+}
+
+__global__ void k_class_root(const double* __restrict__ xs, int64_t n, double Lz, int P, int p,
+                             int K, int32_t* __restrict__ cls) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    cls[s] = root_bin(xs[3 * s + 2], Lz, P) == p ? 0 : K + 1;
+}
+
+// BFS level h: an atom outside the set joins at level h if a neighbour has a
+// level below h (pull form over the symmetric edge set, double-buffered).
+__global__ void k_class_hop(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            int64_t n, int h, int K, const int32_t* __restrict__ cur,
+                            int32_t* __restrict__ nxt) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int c = cur[s];
+    if (c > K) {
+        for (int64_t e = row_ptr[s]; e < row_ptr[s + 1]; ++e)
+            if (cur[col[e]] < h) { c = h; break; }
+    }
+    nxt[s] = c;
+}
+
+__global__ void k_flag_class(const int32_t* __restrict__ cls, int64_t n, int m,
+                             int32_t* __restrict__ flag) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    flag[s] = cls[s] == m ? 1 : 0;
+}
+
+// Place the atoms of class m after those of classes < m, keeping cell order.
+__global__ void k_place_class(const int32_t* __restrict__ cls, const int32_t* __restrict__ pre,
+                              int64_t n, int m, int32_t base, int32_t* __restrict__ gid,
+                              uint8_t* __restrict__ lroot, int32_t* __restrict__ g2l) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n || cls[s] != m) return;
+    const int l = base + pre[s];
+    gid[l] = (int32_t)s;
+    lroot[l] = m == 0 ? 1 : 0;
+    g2l[s] = l;
+}
+
 __global__ void k_plan_export(const int32_t* __restrict__ gid, const uint8_t* __restrict__ root,
                               const int32_t* __restrict__ perm, int64_t n_ext,
                               int32_t* __restrict__ out_gid, uint8_t* __restrict__ out_root) {
@@ -119,6 +140,7 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
         return MP_ERR_ARG;
     cudaStream_t st = ctx->stream;
     const int64_t n = g.n;
+    const int K = k_hops;
     plan.n_parts = n_parts;
     plan.k_hops = k_hops;
     plan.mode = mode;
@@ -126,76 +148,87 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
     plan.parts.resize(n_parts);
     Workspace& ws = ctx->ws;
     TimerScope ts(ctx, MP_TIMER_PARTITION, 0, n);
-    // scratch: flag[n], flag2[n], pre[n+1], g2l[n], root[n] bytes
+    // scratch: cls[n], cls2[n], flag[n], pre[n+1], g2l[n]
     DevBuf& scratch = ws.pscr;
-    MP_TRY(scratch.reserve(sizeof(int32_t) * (4 * n + 2) + n + 64));
-    int32_t* flag = scratch.as<int32_t>();
-    int32_t* flag2 = flag + n;
-    int32_t* pre = flag2 + n;
+    MP_TRY(scratch.reserve(sizeof(int32_t) * (5 * n + 4) + 64));
+    int32_t* cls = scratch.as<int32_t>();
+    int32_t* cls2 = cls + n;
+    int32_t* flag = cls2 + n;
+    int32_t* pre = flag + n;
     int32_t* g2l = pre + n + 1;
-    uint8_t* root = reinterpret_cast<uint8_t*>(g2l + n + 1);
     const double* xs = g.xs.as<double>();
     const double Lz = g.box[2];
-    // same operation order as the reference definition: (K * r_c) + 1e-6
-    volatile double kw = (double)k_hops * ctx->model.d.r_cut;
-    const double width = kw + 1e-6;
+    const double rc = ctx->model.d.r_cut;
     int64_t halo_total = 0;
-    int rc = MP_OK;
-    for (int p = 0; p < n_parts && rc == MP_OK; ++p) {
+    for (int p = 0; p < n_parts; ++p) {
         Part& P = plan.parts[p];
-        int32_t* cur = flag;
+        int32_t* cur = cls;
         if (mode == MP_HALO_GEOM) {
-            k_flags_geom<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, width, flag, root); note_launch();
+            k_class_geom<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, rc, K, cls);
+            note_launch();
         } else {
-            k_flags_root<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, flag, root); note_launch();
-            int32_t* other = flag2;
-            for (int h = 0; h < k_hops; ++h) {
-                k_bfs_hop<<<grid_for(n, 256), 256, 0, st>>>(g.row_ptr.as<int64_t>(),
-                                                            g.col.as<int32_t>(), n, cur, other); note_launch();
+            k_class_root<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, K, cls);
+            note_launch();
+            int32_t* other = cls2;
+            for (int h = 1; h <= K; ++h) {
+                k_class_hop<<<grid_for(n, 256), 256, 0, st>>>(g.row_ptr.as<int64_t>(),
+                                                              g.col.as<int32_t>(), n, h, K, cur, other);
+                note_launch();
                 int32_t* t = cur;
                 cur = other;
                 other = t;
             }
         }
-        rc = exclusive_scan_i32(cur, pre, n, ws.tmp, st);
-        if (rc) break;
-        int32_t n_ext32 = 0;
-        if (cudaMemcpyAsync(&n_ext32, pre + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st) ||
-            cudaStreamSynchronize(st)) { rc = MP_ERR_CUDA; break; }
-        P.n_ext = n_ext32;
-        if ((rc = P.gid.reserve(sizeof(int32_t) * (P.n_ext + 1)))) break;
-        if ((rc = P.is_root.reserve(P.n_ext + 16))) break;
-        if ((rc = P.row_ptr.reserve(sizeof(int64_t) * (P.n_ext + 1)))) break;
-        k_compact<<<grid_for(n, 256), 256, 0, st>>>(cur, pre, root, n, P.gid.as<int32_t>(),
-                                                    P.is_root.as<uint8_t>(), g2l); note_launch();
-        int32_t* ldeg = cur == flag ? flag2 : flag;   // free flag buffer
+        // class counts, then a stable placement class by class
+        std::vector<int32_t> counts(K + 1);
+        MP_CUDA_TRY(cudaMemsetAsync(g2l, 0xFF, sizeof(int32_t) * n, st));
+        MP_TRY(P.gid.reserve(sizeof(int32_t) * (n + 1)));
+        MP_TRY(P.is_root.reserve(n + 16));
+        int32_t base = 0;
+        P.n_le.assign(K + 1, 0);
+        for (int m = 0; m <= K; ++m) {
+            k_flag_class<<<grid_for(n, 256), 256, 0, st>>>(cur, n, m, flag);
+            note_launch();
+            MP_TRY(exclusive_scan_i32(flag, pre, n, ws.tmp, st));
+            k_place_class<<<grid_for(n, 256), 256, 0, st>>>(cur, pre, n, m, base,
+                                                            P.gid.as<int32_t>(),
+                                                            P.is_root.as<uint8_t>(), g2l);
+            note_launch();
+            int32_t cnt = 0;
+            MP_CUDA_TRY(cudaMemcpyAsync(&cnt, pre + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            MP_CUDA_TRY(cudaStreamSynchronize(st));
+            counts[m] = cnt;
+            base += cnt;
+            P.n_le[m] = base;
+        }
+        P.n_root = P.n_le[0];
+        P.n_ext = P.n_le[K];
+        MP_TRY(P.row_ptr.reserve(sizeof(int64_t) * (P.n_ext + 1)));
         k_local_deg<<<grid_for(P.n_ext, 256), 256, 0, st>>>(
-            g.row_ptr.as<int64_t>(), g.col.as<int32_t>(), P.gid.as<int32_t>(), g2l, P.n_ext, ldeg); note_launch();
-        rc = exclusive_scan_i64(ldeg, P.row_ptr.as<int64_t>(), P.n_ext, ws.tmp, st);
-        if (rc) break;
+            g.row_ptr.as<int64_t>(), g.col.as<int32_t>(), P.gid.as<int32_t>(), g2l, P.n_ext, flag);
+        note_launch();
+        MP_TRY(exclusive_scan_i64(flag, P.row_ptr.as<int64_t>(), P.n_ext, ws.tmp, st));
         int64_t ne = 0;
-        int32_t nroot = 0;
-        if (cudaMemcpyAsync(&ne, P.row_ptr.as<int64_t>() + P.n_ext, sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, st) ||
-            cudaStreamSynchronize(st)) { rc = MP_ERR_CUDA; break; }
+        MP_CUDA_TRY(cudaMemcpyAsync(&ne, P.row_ptr.as<int64_t>() + P.n_ext, sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, st));
+        MP_CUDA_TRY(cudaStreamSynchronize(st));
         P.n_edges = ne;
-        if ((rc = P.col.reserve(sizeof(int32_t) * (ne + 1)))) break;
-        if ((rc = P.shift.reserve(ne + 16))) break;
+        MP_TRY(P.col.reserve(sizeof(int32_t) * (ne + 1)));
+        MP_TRY(P.shift.reserve(ne + 16));
         k_local_fill<<<grid_for(P.n_ext, 256), 256, 0, st>>>(
             g.row_ptr.as<int64_t>(), g.col.as<int32_t>(), g.shift.as<int8_t>(),
             P.gid.as<int32_t>(), g2l, P.n_ext, P.row_ptr.as<int64_t>(), P.col.as<int32_t>(),
-            P.shift.as<int8_t>()); note_launch();
-        // root count: roots are flagged in `root` (uint8) -> count with a scan of flags
-        k_flags_root<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, ldeg, root); note_launch();
-        rc = exclusive_scan_i32(ldeg, pre, n, ws.tmp, st);
-        if (rc) break;
-        if (cudaMemcpyAsync(&nroot, pre + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st) ||
-            cudaStreamSynchronize(st)) { rc = MP_ERR_CUDA; break; }
-        P.n_root = nroot;
+            P.shift.as<int8_t>());
+        note_launch();
+        // edge counts of the class prefixes (rows are in class order)
+        P.e_le.assign(K + 1, 0);
+        for (int m = 0; m <= K; ++m)
+            MP_CUDA_TRY(cudaMemcpyAsync(&P.e_le[m], P.row_ptr.as<int64_t>() + P.n_le[m],
+                                        sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        MP_CUDA_TRY(cudaStreamSynchronize(st));
         halo_total += P.n_ext - P.n_root;
     }
-    if (rc) return rc;
-    if (cudaGetLastError() != cudaSuccess) return MP_ERR_CUDA;
+    MP_CUDA_TRY(cudaGetLastError());
     if (halo_factor) *halo_factor = (double)halo_total / (double)n;
     return MP_OK;
 }
