@@ -25,8 +25,11 @@
 //   5. thread = channel runs the message (forward) or symmetric-pair adjoint
 //      (backward) epilogue on the slice.  In the adjoint each channel forms
 //      its own share of dE_pair/dd and accumulates it over the receiver row
-//      (compensated); channels are summed once per row in FP64,
+//      (FP32 over a slice, compensated across slices); channels are summed
+//      once per row in FP64,
 //      F_k = sum_e sum_c g_c(e).
+// The MLP's hidden activations use the fast exponential and division: they
+// are rounded to BF16 for the next contraction anyway.
 // One thread issues the MMAs; completion is signalled through an mbarrier
 // whose waits are bounded (clock64): on a timeout the warpgroup sets an
 // error bit, stops, and the CTA frees its tensor memory and returns.
@@ -57,8 +60,15 @@ struct TPaths {
 struct alignas(1024) Tiles {
     __nv_bfloat16 W3[5][128 * 64];   // 5 x 16 KB, one 128-row tile per radial path
     __nv_bfloat16 W2[64 * 64];       // W2 (out, in), K-major
-    float W1[kH * kNB];
+    float W1[kH * kNB + 4];          // hidden 32..63 start 4 floats later (bank offset)
 };
+
+// Row h of W1 in shared memory.
+__device__ __forceinline__ int w1_row(int h) { return h * kNB + (h >= 32 ? 4 : 0); }
+
+// Sigmoid with the fast exponential and division: the MLP activations feed
+// BF16 tiles, whose rounding (2^-9) dwarfs their error.
+__device__ __forceinline__ float sigmoid_fast(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
 
 struct alignas(1024) WgState {
     __nv_bfloat16 B[128 * 64];       // a1 tile, then a2 tile, of the super-chunk
@@ -138,7 +148,7 @@ __device__ __forceinline__ void tc_setup(SmemTC& s, const LayerW& wl, int np, bo
         uint4* dst = reinterpret_cast<uint4*>(s.t.W3[p]);
         for (int q = tid; q < 128 * 64 * 2 / 16; q += NTH) dst[q] = __ldg(&src[q]);
     }
-    for (int q = tid; q < kH * kNB; q += NTH) s.t.W1[q] = __ldg(&wl.W1[q]);
+    for (int q = tid; q < kH * kNB; q += NTH) s.t.W1[w1_row(q / kNB) + q % kNB] = __ldg(&wl.W1[q]);
     if ((tid & 127) == 0) {
         tc::mbar_init(&s.wg[tid >> 7].mbar, 1);
         s.wg[tid >> 7].abort = 0;
@@ -163,7 +173,7 @@ __device__ __forceinline__ void tc_teardown(SmemTC& s, uint32_t phase, int* err,
     if ((tid >> 5) == 0) tc::tmem_dealloc<TM_COLS>(s.taddr);
 }
 
-// Geometry of edge e: eps (and d eps/dr), Y_lm (lm >= 1), unit vector, r.
+// Geometry of edge e: eps (and d eps/dr), Y_lm (lm >= 1), unit vector, 1 / r.
 template <bool DERIV>
 __device__ __forceinline__ int edge_geometry(const EdgeArgs& a, const int64_t* rp, int64_t e,
                                              int64_t e_end, int64_t r0, int nrows, float eps[kNB],
@@ -174,7 +184,7 @@ __device__ __forceinline__ int edge_geometry(const EdgeArgs& a, const int64_t* r
 #pragma unroll
         for (int q = 0; q < TNLM; ++q) Y[q] = 0.f;
         u4[0] = u4[1] = u4[2] = 0.f;
-        u4[3] = 1.f;
+        u4[3] = 1.f;   // 1 / r
         col = 0;
         return -1;
     }
@@ -187,7 +197,7 @@ __device__ __forceinline__ int edge_geometry(const EdgeArgs& a, const int64_t* r
     u4[0] = d[0] * ir;
     u4[1] = d[1] * ir;
     u4[2] = d[2] * ir;
-    u4[3] = r;
+    u4[3] = ir;
     float env, denv;
     radial_basis<DERIV>(r, a.k, eps, deps, env, denv);
     sph_harm<TLMAX>(u4, Y);
@@ -239,15 +249,15 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
                 w.col[lt] = col;
 #pragma unroll
                 for (int q = 1; q < TNLM; ++q) w.Y[lt][q - 1] = Y[q];
-#pragma unroll
+#pragma unroll 1
                 for (int j = 0; j < 8; ++j) {
                     float v[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         float z = 0.f;
 #pragma unroll
-                        for (int b = 0; b < kNB; ++b) z = fmaf(s.t.W1[(8 * j + q) * kNB + b], eps[b], z);
-                        v[q] = silu(z);
+                        for (int b = 0; b < kNB; ++b) z = fmaf(s.t.W1[w1_row(8 * j + q) + b], eps[b], z);
+                        v[q] = z * sigmoid_fast(z);
                     }
                     st_row_chunk(w.B, lt, j, v);
                 }
@@ -267,7 +277,7 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
                 tc::tmem_ld16(tl + 16 * h, z);
                 tc::tmem_wait_ld();
 #pragma unroll
-                for (int q = 0; q < 16; ++q) z[q] = silu(z[q]);
+                for (int q = 0; q < 16; ++q) z[q] = z[q] * sigmoid_fast(z[q]);
                 st_row_chunk(w.B, lt, 2 * h, z);
                 st_row_chunk(w.B, lt, 2 * h + 1, z + 8);
             }
@@ -392,7 +402,19 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
         wg_sync(g);
         const int64_t e_beg = w.rp[0], e_end = w.rp[nrows];
         float gacc[TNLM], ak[TNLM], hk[TNLM];
-        float fk[3] = {0.f, 0.f, 0.f}, fc[3] = {0.f, 0.f, 0.f};   // compensated row force
+        // this channel's share of the row force: FP32 partial sums over a slice
+        // (fs), folded into a compensated row sum (fk, fc) once per slice
+        float fk[3] = {0.f, 0.f, 0.f}, fc[3] = {0.f, 0.f, 0.f}, fs[3] = {0.f, 0.f, 0.f};
+        auto fold = [&]() {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float y = fs[q] - fc[q];
+                const float t = fk[q] + y;
+                fc[q] = (t - fk[q]) - y;
+                fk[q] = t;
+                fs[q] = 0.f;
+            }
+        };
 #pragma unroll
         for (int q = 0; q < TNLM; ++q) gacc[q] = ak[q] = hk[q] = 0.f;
         int cur = -1, next = 0;
@@ -430,29 +452,39 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                 for (int q = 0; q < 4; ++q) w.u[lt][q] = u4[q];
             }
             wg_sync(g);
-            {   // tile row lt: a1 of edge lt / 2, or (odd rows) its r-tangent
+            {   // tile rows 2 e (a1 of edge e) and 2 e + 1 (its r-tangent): each lane of
+                // the pair forms z1 and dz1 for half of the hidden units, evaluates
+                // both rows' activations there and swaps the half its partner needs
                 const int e = lt >> 1, t = lt & 1;
-                float src[kNB];
+                float src[kNB], dsrc[kNB];
 #pragma unroll
-                for (int b = 0; b < kNB; ++b) src[b] = w.eps[e][b];
-                float dsrc[kNB];
-#pragma unroll
-                for (int b = 0; b < kNB; ++b) dsrc[b] = t ? w.deps[e][b] : 0.f;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    float v[8];
+                for (int b = 0; b < kNB; ++b) {
+                    src[b] = w.eps[e][b];
+                    dsrc[b] = w.deps[e][b];
+                }
+#pragma unroll 1
+                for (int j = 0; j < 4; ++j) {
+                    float keep[8], give[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
+                        const float* wr = s.t.W1 + w1_row(32 * t + 8 * j + q);
                         float z = 0.f, dz = 0.f;
 #pragma unroll
                         for (int b = 0; b < kNB; ++b) {
-                            const float wv = s.t.W1[(8 * j + q) * kNB + b];
-                            z = fmaf(wv, src[b], z);
-                            dz = fmaf(wv, dsrc[b], dz);
+                            z = fmaf(wr[b], src[b], z);
+                            dz = fmaf(wr[b], dsrc[b], dz);
                         }
-                        v[q] = t ? silu_grad(z) * dz : silu(z);
+                        const float sg = sigmoid_fast(z);
+                        const float val = z * sg;
+                        const float tan = sg * fmaf(z, 1.f - sg, 1.f) * dz;
+                        keep[q] = t ? tan : val;
+                        give[q] = t ? val : tan;
                     }
-                    st_row_chunk(w.B, lt, j, v);
+                    float got[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) got[q] = __shfl_xor_sync(0xffffffffu, give[q], 1);
+                    st_row_chunk(w.B, lt, 4 * t + j, keep);
+                    st_row_chunk(w.B, lt, 4 * (1 - t) + j, got);
                 }
             }
             tc::fence_proxy_async();
@@ -472,7 +504,8 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const float zv = __shfl_sync(0xffffffffu, z[q], lane & ~1);
-                    z[q] = (lane & 1) ? silu_grad(zv) * z[q] : silu(z[q]);
+                    const float sg = sigmoid_fast(zv);
+                    z[q] = (lane & 1) ? sg * fmaf(zv, 1.f - sg, 1.f) * z[q] : zv * sg;
                 }
                 st_row_chunk(w.B, lt, 2 * h, z);
                 st_row_chunk(w.B, lt, 2 * h + 1, z + 8);
@@ -520,6 +553,7 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                     }
                     if (lr != cur) {
                         if (cur >= 0) {
+                            fold();
                             flush(cur, true);
                             next = cur + 1;
                         }
@@ -538,74 +572,78 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                     }
                     tc::tmem_wait_ld();
                     float Y[TNLM];
-                    Y[0] = 1.f;
-#pragma unroll
-                    for (int q = 1; q < TNLM; ++q) Y[q] = w.Y[e][q - 1];
-                    if (!FIRST) {
-                        float g0 = R[0] * ajc[0];
-                        float sm1 = 0.f, sm2 = 0.f;
-#pragma unroll
-                        for (int m = 0; m < 3; ++m) {
-                            sm1 = fmaf(ajc[1 + m], Y[1 + m], sm1);
-                            gacc[1 + m] = fmaf(R[PP::slb(1)], ajc[1 + m], gacc[1 + m]);
-                        }
-#pragma unroll
-                        for (int m = 0; m < 5; ++m) {
-                            sm2 = fmaf(ajc[4 + m], Y[4 + m], sm2);
-                            gacc[4 + m] = fmaf(R[PP::slb(2)], ajc[4 + m], gacc[4 + m]);
-                        }
-                        g0 = fmaf(-R[PP::sla(1)], sm1, g0);
-                        g0 = fmaf(R[PP::sla(2)], sm2, g0);
-                        gacc[0] += g0;
+                    {
+                        const float4 y0 = *reinterpret_cast<const float4*>(&w.Y[e][0]);
+                        const float4 y1 = *reinterpret_cast<const float4*>(&w.Y[e][4]);
+                        Y[0] = 1.f;
+                        Y[1] = y0.x; Y[2] = y0.y; Y[3] = y0.z; Y[4] = y0.w;
+                        Y[5] = y1.x; Y[6] = y1.y; Y[7] = y1.z; Y[8] = y1.w;
                     }
-                    // this channel's share of dE_pair/dd: radial part along u and
-                    // the angular part through dE/dY
-                    float gr = (ak[0] * hjc[0] + ajc[0] * hk[0]) * dR[0];
+                    // Y-weighted sums of the sender's (j) and receiver's (k) alpha
+                    float sj1 = 0.f, sk1 = 0.f, sj2 = 0.f, sk2 = 0.f;
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        sj1 = fmaf(ajc[1 + m], Y[1 + m], sj1);
+                        sk1 = fmaf(ak[1 + m], Y[1 + m], sk1);
+                    }
+#pragma unroll
+                    for (int m = 0; m < 5; ++m) {
+                        sj2 = fmaf(ajc[4 + m], Y[4 + m], sj2);
+                        sk2 = fmaf(ak[4 + m], Y[4 + m], sk2);
+                    }
+                    if (!FIRST) {   // dE/dh_k as the sender of the reverse edge (i <- k)
+                        float g0 = R[0] * ajc[0];
+                        g0 = fmaf(-R[PP::sla(1)], sj1, g0);
+                        g0 = fmaf(R[PP::sla(2)], sj2, g0);
+                        gacc[0] += g0;
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) gacc[1 + m] = fmaf(R[PP::slb(1)], ajc[1 + m], gacc[1 + m]);
+#pragma unroll
+                        for (int m = 0; m < 5; ++m) gacc[4 + m] = fmaf(R[PP::slb(2)], ajc[4 + m], gacc[4 + m]);
+                    }
+                    // this channel's share of dE_pair/dd: radial part along u (both
+                    // directions' dE/dR contracted with dR/dr) and the angular part
+                    // through dE/dY; the l = 1 term of the reverse edge changes sign
+                    const float hj0 = hjc[0], hk0 = hk[0];
+                    float gr = fmaf(ak[0], hj0, ajc[0] * hk0) * dR[0];
+                    gr = fmaf(fmaf(hj0, sk1, -hk0 * sj1), dR[PP::sla(1)], gr);
+                    gr = fmaf(fmaf(hj0, sk2, hk0 * sj2), dR[PP::sla(2)], gr);
+                    if (!FIRST) {
+                        float g1b = 0.f, g2b = 0.f;
+#pragma unroll
+                        for (int m = 0; m < 3; ++m)
+                            g1b = fmaf(ak[1 + m], hjc[1 + m], fmaf(ajc[1 + m], hk[1 + m], g1b));
+#pragma unroll
+                        for (int m = 0; m < 5; ++m)
+                            g2b = fmaf(ak[4 + m], hjc[4 + m], fmaf(ajc[4 + m], hk[4 + m], g2b));
+                        gr = fmaf(g1b, dR[PP::slb(1)], gr);
+                        gr = fmaf(g2b, dR[PP::slb(2)], gr);
+                    }
                     float gy[TNLM];
                     gy[0] = 0.f;
                     {
-                        float g1a = 0.f, g1b = 0.f;
+                        const float a1 = R[PP::sla(1)] * hj0, b1 = R[PP::sla(1)] * hk0;
+                        const float a2 = R[PP::sla(2)] * hj0, b2 = R[PP::sla(2)] * hk0;
 #pragma unroll
-                        for (int m = 0; m < 3; ++m) {
-                            const float t = ak[1 + m] * hjc[0] - ajc[1 + m] * hk[0];
-                            g1a = fmaf(Y[1 + m], t, g1a);
-                            gy[1 + m] = R[PP::sla(1)] * t;
-                            if (!FIRST) g1b += ak[1 + m] * hjc[1 + m] + ajc[1 + m] * hk[1 + m];
-                        }
-                        gr = fmaf(g1a, dR[PP::sla(1)], gr);
-                        if (!FIRST) gr = fmaf(g1b, dR[PP::slb(1)], gr);
-                    }
-                    {
-                        float g2a = 0.f, g2b = 0.f;
+                        for (int m = 0; m < 3; ++m) gy[1 + m] = fmaf(ak[1 + m], a1, -ajc[1 + m] * b1);
 #pragma unroll
-                        for (int m = 0; m < 5; ++m) {
-                            const float t = ak[4 + m] * hjc[0] + ajc[4 + m] * hk[0];
-                            g2a = fmaf(Y[4 + m], t, g2a);
-                            gy[4 + m] = R[PP::sla(2)] * t;
-                            if (!FIRST) g2b += ak[4 + m] * hjc[4 + m] + ajc[4 + m] * hk[4 + m];
-                        }
-                        gr = fmaf(g2a, dR[PP::sla(2)], gr);
-                        if (!FIRST) gr = fmaf(g2b, dR[PP::slb(2)], gr);
+                        for (int m = 0; m < 5; ++m) gy[4 + m] = fmaf(ak[4 + m], a2, ajc[4 + m] * b2);
                     }
-                    const float u[3] = {w.u[e][0], w.u[e][1], w.u[e][2]};
-                    const float ir = 1.f / w.u[e][3];
+                    const float4 ue = *reinterpret_cast<const float4*>(&w.u[e][0]);
+                    const float u[3] = {ue.x, ue.y, ue.z};
+                    const float ir = ue.w;
                     float v[3];
                     sph_grad<TLMAX, float>(u, gy, v);
                     const float vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const float gq = gr * u[q] + (v[q] - vu * u[q]) * ir;
-                        const float y = gq - fc[q];
-                        const float t = fk[q] + y;
-                        fc[q] = (t - fk[q]) - y;
-                        fk[q] = t;
-                    }
+                    for (int q = 0; q < 3; ++q) fs[q] += fmaf(gr, u[q], (v[q] - vu * u[q]) * ir);
 #pragma unroll
                     for (int q = 0; q < TNLM; ++q) {
                         ajc[q] = ajn[q];
                         hjc[q] = hjn[q];
                     }
                 }
+                fold();
                 tc::fence_before_sync();
                 wg_sync(g);
                 if (lt == 0 && sl + 1 < SCB / 8) {
