@@ -93,7 +93,7 @@ static int upload_model(Model& m, const double* w) {
     auto takeh = [&](size_t k) { size_t o = nh; nh += (k + 63) / 64 * 64; return o; };
     size_t o_emb = takef((size_t)S * F), o_e0 = takef(S), o_wout = takef(F),
            o_head = takef((size_t)Hh * F + 2 * Hh + 1);
-    struct LO { size_t W1, W2, W2T, W3, W3T, W0, W0T, U[2], UT[2], b, V[2], VT[2]; size_t W2b, W3b, W3Tb, W2Tb, W2sw, W3sw; };
+    struct LO { size_t W1, W2, W2T, W3, W3T, W0, W0T, U[2], UT[2], b, V[2], VT[2]; size_t W2b, W3b, W3Tb, W2Tb, W2sw, W3sw, NswF; };
     const bool tc_shape = (F == 128 && lm == 2 && H == 64);
     std::vector<LO> lo(L);
     for (int t = 0; t < L; ++t) {
@@ -117,6 +117,7 @@ static int upload_model(Model& m, const double* w) {
         lo[t].W2Tb = takeh((size_t)H * H);
         lo[t].W2sw = tc_shape ? takeh((size_t)128 * H) : 0;
         lo[t].W3sw = tc_shape ? takeh((size_t)P * H) : 0;
+        lo[t].NswF = tc_shape ? takeh((size_t)5 * F * F) : 0;
     }
     std::vector<float> hf(nf, 0.f);
     std::vector<__nv_bfloat16> hh(nh > 0 ? nh : 1);
@@ -166,6 +167,14 @@ static int upload_model(Model& m, const double* w) {
                     for (int k = 0; k < H; ++k)
                         put(lo[t].W3sw + (size_t)tile * 128 * H, r, k,
                             hf[lo[t].W3 + (size_t)(tile * 128 + r) * H + k]);
+            // node matrices: K-block kb of matrix g at (2 g + kb) * 128 * 64
+            const size_t mats[5] = {lo[t].W0, lo[t].U[0], lo[t].U[1], lo[t].V[0], lo[t].V[1]};
+            for (int g = 0; g < 5; ++g)
+                for (int r = 0; r < F; ++r)
+                    for (int k = 0; k < F; ++k) {
+                        const size_t blk = (size_t)(2 * g + k / 64) * 128 * 64;
+                        put(lo[t].NswF + blk, r, k % 64, hf[mats[g] + (size_t)r * F + k]);
+                    }
         }
     }
     const size_t fbytes = nf * sizeof(float), hbytes = hh.size() * sizeof(__nv_bfloat16);
@@ -202,6 +211,7 @@ static int upload_model(Model& m, const double* w) {
         q.W2Tb = hbase + lo[t].W2Tb;
         q.W2sw = tc_shape ? hbase + lo[t].W2sw : nullptr;
         q.W3sw = tc_shape ? hbase + lo[t].W3sw : nullptr;
+        q.NswF = tc_shape ? hbase + lo[t].NswF : nullptr;
     }
     return MP_OK;
 }

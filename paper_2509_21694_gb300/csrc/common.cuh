@@ -62,6 +62,9 @@ struct LayerW {
     // W3 as (1 + 2 lmax) tiles of 128 rows (one per radial path).
     __nv_bfloat16* W2sw;
     __nv_bfloat16* W3sw;
+    // Node-update operand image (F = 128): [W0, U1, U2, V1, V2] (out, in),
+    // each two K-blocks of 64 in the same swizzled layout.
+    __nv_bfloat16* NswF;
 };
 
 struct Model {

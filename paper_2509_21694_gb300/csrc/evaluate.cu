@@ -288,6 +288,7 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
     ea.err = ctx->ws.err.as<int>();
     NodeArgs na{};
     na.inv_navg = kc.inv_navg;
+    na.err = ctx->ws.err.as<int>();
     // Forward: layer t only needs outputs within K-1-t hops of a root; the
     // rest of the next feature array is set to zero (never multiplied by a
     // nonzero coefficient, but kept finite).
@@ -314,7 +315,10 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         na.last = t == K - 1;
         {
             TimerScope ts(ctx, MP_TIMER_NODE_FWD, 0, rows);
-            MP_TRY(launch_node_fwd_f32(m, na, st));
+            if (precision == MP_BF16)
+                MP_TRY(launch_node_fwd_bf16(m, na, st, ctx->num_sms));
+            else
+                MP_TRY(launch_node_fwd_f32(m, na, st));
         }
         if (rows < n)
             MP_CUDA_TRY(cudaMemsetAsync(b.H + (t + 1) * feat + rows * row_f, 0,
@@ -357,7 +361,7 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         na.last = t == K - 1;
         {
             TimerScope ts(ctx, MP_TIMER_NODE_BWD, 0, nrows);
-            MP_TRY(launch_node_bwd_f32(m, na, st));
+            MP_TRY(launch_node_bwd_f32(m, na, st));   // FP32 in both precisions (linear adjoint)
         }
         if (nrows < n)
             MP_CUDA_TRY(cudaMemsetAsync(b.alpha + nrows * row_f, 0,

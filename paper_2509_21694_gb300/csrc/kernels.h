@@ -44,9 +44,12 @@ struct NodeArgs {
     float* Alpha;        // adjoint output (/N_avg)
     float inv_navg;
     bool last;
+    int* err;            // device error bits (tensor-core kernels)
 };
 int launch_node_fwd_f32(const Model& m, const NodeArgs& a, cudaStream_t st);
 int launch_node_bwd_f32(const Model& m, const NodeArgs& a, cudaStream_t st);
+// BF16 operands on tcgen05 (F = 128, lmax = 2), forward only.
+int launch_node_fwd_bf16(const Model& m, const NodeArgs& a, cudaStream_t st, int num_sms);
 
 // Tangent (forward-mode) pass of one layer along a displacement field v.
 struct TangentArgs {

@@ -135,6 +135,14 @@ __device__ __forceinline__ void tmem_ld2(uint32_t taddr, float v[2]) {
     v[1] = __uint_as_float(r1);
 }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float v[4]) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(taddr));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = __uint_as_float(r[q]);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     uint32_t r[16];
     asm volatile(
