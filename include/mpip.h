@@ -146,7 +146,7 @@ int mp_plan_info(const mp_plan* plan, int p, int64_t* n_ext, int64_t* n_root, in
  * d_gid int32 [n_ext], d_is_root uint8 [n_ext].  Order: by hop class
  * (roots first, then halo atoms nearer than r_c + s_1, 2 r_c + s_2, ...,
  * with s_K = 1e-6 and s_m = 1e-6 m / K; for MP_HALO_BFS the BFS level),
- * ascending cell order within a class.  Layer t of a K-layer evaluation
+ * within a class the cells in Morton order of their grid coordinates.  Layer t of a K-layer evaluation
  * computes only the classes <= K-1-t it needs. */
 int mp_plan_export(const mp_plan* plan, int p, int32_t* d_gid, uint8_t* d_is_root);
 void mp_plan_free(mp_plan* plan);

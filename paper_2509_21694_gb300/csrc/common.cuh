@@ -118,7 +118,8 @@ struct SubSys {
 
 struct Workspace {
     DevBuf xl, sp, H, A, S, G0, G1, alpha, floc, eatom, esum, fsum, ebuf,
-        err, tmp, xw, perm_pos, pscr, red, headbuf, adam;
+        err, tmp, xw, perm_pos, pscr, red, headbuf, adam, sched,
+        corder;   // partition placement: cells in Morton order [ncell], sizes, offsets
 };
 
 }  // namespace mp
@@ -148,6 +149,7 @@ struct mp_ctx {
     int num_sms = 0;
     mp::Workspace ws;
     int* h_err = nullptr;      // pinned host word for error read-back
+    int corder_nc[3] = {0, 0, 0};   // cell grid the cached Morton order belongs to
 };
 
 struct mp_graph {

@@ -79,9 +79,11 @@ struct alignas(1024) WgState {
     int row[SCF], col[SCF];
     double fpart[RPG][4][3];         // per-row, per-warp force partial sums
     int64_t rp[RPG + 1];
+    int64_t next_grp;                // next row group, fetched by the leader
     uint64_t mbar;
     int abort;
 };
+
 
 struct SmemTC {
     Tiles t;
@@ -96,6 +98,15 @@ __device__ __forceinline__ SmemTC& smem_tc(unsigned char* raw) {
 
 __device__ __forceinline__ void wg_sync(int g) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(128) : "memory");
+}
+
+// Row groups are handed out dynamically: each warpgroup starts at its own
+// index and then takes the next unclaimed group from a global counter, so
+// warpgroups that drew light groups keep working until the list is done.
+__device__ __forceinline__ int64_t next_group(WgState& w, const EdgeArgs& a, int g, int lt) {
+    if (lt == 0) w.next_grp = (int64_t)gridDim.x * NWG + atomicAdd(a.sched, 1);
+    wg_sync(g);
+    return w.next_grp;
 }
 
 __device__ __forceinline__ int find_row_t(const int64_t* rp, int nrows, int64_t e) {
@@ -224,7 +235,7 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
     bool alive = true;
 
     for (int64_t grp = (int64_t)blockIdx.x * NWG + g; grp < n_groups && alive;
-         grp += (int64_t)gridDim.x * NWG) {
+         grp = next_group(w, a, g, lt)) {
         const int64_t r0 = grp * RPG;
         const int nrows = (int)min((int64_t)RPG, a.n - r0);
         if (lt <= nrows) w.rp[lt] = a.row_ptr[r0 + lt];
@@ -394,7 +405,7 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
     bool alive = true;
 
     for (int64_t grp = (int64_t)blockIdx.x * NWG + g; grp < n_groups && alive;
-         grp += (int64_t)gridDim.x * NWG) {
+         grp = next_group(w, a, g, lt)) {
         const int64_t r0 = grp * RPG;
         const int nrows = (int)min((int64_t)RPG, a.n - r0);
         if (lt <= nrows) w.rp[lt] = a.row_ptr[r0 + lt];
@@ -681,6 +692,7 @@ int launch_tc(K kernel, const EdgeArgs& a, int num_sms, cudaStream_t st) {
     int64_t grid = (int64_t)num_sms;   // one CTA (one 512-column TMEM allocation) per SM
     const int64_t need = (groups + NWG - 1) / NWG;
     if (grid > need) grid = need;
+    MP_CUDA_TRY(cudaMemsetAsync(a.sched, 0, sizeof(int), st));
     kernel<<<(unsigned)grid, NTH, smem, st>>>(a, *a.w, groups, a.err);
     note_launch();
     MP_CUDA_TRY(cudaGetLastError());
@@ -690,14 +702,14 @@ int launch_tc(K kernel, const EdgeArgs& a, int num_sms, cudaStream_t st) {
 }  // namespace
 
 int launch_edge_fwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int num_sms) {
-    if (!(m.d.F == TF && m.d.lmax == TLMAX) || !a.w->W3sw || !a.err) return MP_ERR_UNSUPPORTED;
+    if (!(m.d.F == TF && m.d.lmax == TLMAX) || !a.w->W3sw || !a.err || !a.sched) return MP_ERR_UNSUPPORTED;
     if (a.n == 0) return MP_OK;
     return a.first ? launch_tc(k_edge_fwd_tc<true>, a, num_sms, st)
                    : launch_tc(k_edge_fwd_tc<false>, a, num_sms, st);
 }
 
 int launch_edge_bwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int num_sms) {
-    if (!(m.d.F == TF && m.d.lmax == TLMAX) || !a.w->W3sw || !a.err) return MP_ERR_UNSUPPORTED;
+    if (!(m.d.F == TF && m.d.lmax == TLMAX) || !a.w->W3sw || !a.err || !a.sched) return MP_ERR_UNSUPPORTED;
     if (a.n == 0) return MP_OK;
     return a.first ? launch_tc(k_edge_bwd_tc<true>, a, num_sms, st)
                    : launch_tc(k_edge_bwd_tc<false>, a, num_sms, st);

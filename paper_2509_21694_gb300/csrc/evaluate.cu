@@ -286,6 +286,7 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
     ea.k = kc;
     ea.seed = ss.is_root;
     ea.err = ctx->ws.err.as<int>();
+    ea.sched = ctx->ws.sched.as<int>();
     NodeArgs na{};
     na.inv_navg = kc.inv_navg;
     na.err = ctx->ws.err.as<int>();
@@ -437,6 +438,7 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
     MP_TRY(ws.floc.reserve(sizeof(double) * 3 * nmax));
     MP_TRY(ws.eatom.reserve(sizeof(double) * nmax));
     MP_TRY(ws.err.reserve(64));
+    MP_TRY(ws.sched.reserve(64));
     MP_CUDA_TRY(cudaMemsetAsync(ws.err.as<int>(), 0, sizeof(int), st));
 
     EvalBufs b;

@@ -24,6 +24,7 @@ struct EdgeArgs {
     double* frc;              // adjoint: [n][3] forces, accumulated
     bool first;               // layer 0: input l >= 1 features are zero
     int* err;                 // device error word (bit 2: bounded wait timed out)
+    int* sched;               // tensor-core kernels: row-group counter (zeroed per launch)
 };
 
 int launch_edge_fwd_f32(const Model& m, const EdgeArgs& a, cudaStream_t st);

@@ -8,8 +8,12 @@
 // r_c).  The extended set keeps ascending cell order, so each local row holds
 // the global row's edges in the same order, filtered to senders in the set.
 // Local atoms are ordered by hop class (roots, then atoms within r_c of the
-// slab or one hop of a root, ...), each class in cell order, so the rows a
-// layer needs form a prefix of the local numbering.
+// slab or one hop of a root, ...), each class in Morton order of the cells,
+// so the rows a layer needs form a prefix of the local numbering.
+#include <algorithm>
+#include <utility>
+#include <vector>
+
 #include "common.cuh"
 
 namespace mp {
@@ -104,21 +108,44 @@ __global__ void k_class_hop(const int64_t* __restrict__ row_ptr, const int32_t* 
     nxt[s] = c;
 }
 
-__global__ void k_flag_class(const int32_t* __restrict__ cls, int64_t n, int m,
-                             int32_t* __restrict__ flag) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    flag[s] = cls[s] == m ? 1 : 0;
+// Atom order used for placement: cells in Morton order of their grid
+// coordinates, the atoms of a cell in sorted order.  bperm[pos] = atom.
+__global__ void k_cell_sizes(const int32_t* __restrict__ cell_start,
+                             const int32_t* __restrict__ corder, int ncell,
+                             int32_t* __restrict__ sz) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ncell) return;
+    const int c = corder[k];
+    sz[k] = cell_start[c + 1] - cell_start[c];
 }
 
-// Place the atoms of class m after those of classes < m, keeping cell order.
-__global__ void k_place_class(const int32_t* __restrict__ cls, const int32_t* __restrict__ pre,
-                              int64_t n, int m, int32_t base, int32_t* __restrict__ gid,
-                              uint8_t* __restrict__ lroot, int32_t* __restrict__ g2l) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n || cls[s] != m) return;
-    const int l = base + pre[s];
-    gid[l] = (int32_t)s;
+__global__ void k_bperm(const int32_t* __restrict__ cell_start, const int32_t* __restrict__ corder,
+                        const int32_t* __restrict__ boff, int ncell, int32_t* __restrict__ bperm) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ncell) return;
+    const int c = corder[k];
+    const int s0 = cell_start[c], cnt = cell_start[c + 1] - s0, o = boff[k];
+    for (int q = 0; q < cnt; ++q) bperm[o + q] = s0 + q;
+}
+
+__global__ void k_flag_class(const int32_t* __restrict__ cls, const int32_t* __restrict__ bperm,
+                             int64_t n, int m, int32_t* __restrict__ flag) {
+    int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= n) return;
+    flag[pos] = cls[bperm[pos]] == m ? 1 : 0;
+}
+
+// Place the atoms of class m after those of classes < m, in placement order.
+__global__ void k_place_class(const int32_t* __restrict__ cls, const int32_t* __restrict__ bperm,
+                              const int32_t* __restrict__ pre, int64_t n, int m, int32_t base,
+                              int32_t* __restrict__ gid, uint8_t* __restrict__ lroot,
+                              int32_t* __restrict__ g2l) {
+    int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= n) return;
+    const int s = bperm[pos];
+    if (cls[s] != m) return;
+    const int l = base + pre[pos];
+    gid[l] = s;
     lroot[l] = m == 0 ? 1 : 0;
     g2l[s] = l;
 }
@@ -130,6 +157,28 @@ __global__ void k_plan_export(const int32_t* __restrict__ gid, const uint8_t* __
     if (l >= n_ext) return;
     out_gid[l] = perm[gid[l]];
     out_root[l] = root[l];
+}
+
+// Cells of an nc[0] x nc[1] x nc[2] grid (id = (z nc1 + y) nc0 + x) sorted by
+// the Morton code of (x, y, z): bit b of x, y, z lands at bits 3b, 3b+1, 3b+2.
+std::vector<int32_t> morton_cell_order(const int nc[3]) {
+    const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    std::vector<std::pair<uint64_t, int32_t>> key(ncell);
+    for (int z = 0; z < nc[2]; ++z)
+        for (int y = 0; y < nc[1]; ++y)
+            for (int x = 0; x < nc[0]; ++x) {
+                uint64_t k = 0;
+                for (int b = 0; b < 21; ++b)
+                    k |= (((uint64_t)(x >> b) & 1u) << (3 * b)) |
+                         (((uint64_t)(y >> b) & 1u) << (3 * b + 1)) |
+                         (((uint64_t)(z >> b) & 1u) << (3 * b + 2));
+                const int32_t id = (z * nc[1] + y) * nc[0] + x;
+                key[id] = {k, id};
+            }
+    std::sort(key.begin(), key.end());
+    std::vector<int32_t> order(ncell);
+    for (int64_t q = 0; q < ncell; ++q) order[q] = key[q].second;
+    return order;
 }
 
 }  // namespace
@@ -148,14 +197,40 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
     plan.parts.resize(n_parts);
     Workspace& ws = ctx->ws;
     TimerScope ts(ctx, MP_TIMER_PARTITION, 0, n);
-    // scratch: cls[n], cls2[n], flag[n], pre[n+1], g2l[n]
+    // scratch: cls[n], cls2[n], flag[n], pre[n+1], g2l[n], bperm[n]
     DevBuf& scratch = ws.pscr;
-    MP_TRY(scratch.reserve(sizeof(int32_t) * (5 * n + 4) + 64));
+    MP_TRY(scratch.reserve(sizeof(int32_t) * (6 * n + 4) + 64));
     int32_t* cls = scratch.as<int32_t>();
     int32_t* cls2 = cls + n;
     int32_t* flag = cls2 + n;
     int32_t* pre = flag + n;
     int32_t* g2l = pre + n + 1;
+    int32_t* bperm = g2l + n + 1;
+    // Placement order: Morton order of cells (cached per grid), so that the
+    // rows in flight together in the edge kernels are a compact region and
+    // their senders' features fit in L2 better than a z-slowest sweep's.
+    const int ncell = g.nc[0] * g.nc[1] * g.nc[2];
+    if (ctx->corder_nc[0] != g.nc[0] || ctx->corder_nc[1] != g.nc[1] ||
+        ctx->corder_nc[2] != g.nc[2]) {
+        const std::vector<int32_t> order = morton_cell_order(g.nc);
+        MP_TRY(ws.corder.reserve(sizeof(int32_t) * (3 * (size_t)ncell + 4)));
+        MP_CUDA_TRY(cudaMemcpyAsync(ws.corder.as<int32_t>(), order.data(),
+                                    sizeof(int32_t) * ncell, cudaMemcpyHostToDevice, st));
+        MP_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int a = 0; a < 3; ++a) ctx->corder_nc[a] = g.nc[a];
+    }
+    {
+        const int32_t* corder = ws.corder.as<int32_t>();
+        int32_t* csz = ws.corder.as<int32_t>() + ncell;
+        int32_t* coff = csz + ncell + 1;
+        k_cell_sizes<<<grid_for(ncell, 256), 256, 0, st>>>(g.cell_start.as<int32_t>(), corder,
+                                                             ncell, csz);
+        note_launch();
+        MP_TRY(exclusive_scan_i32(csz, coff, ncell, ws.tmp, st));
+        k_bperm<<<grid_for(ncell, 128), 128, 0, st>>>(g.cell_start.as<int32_t>(), corder, coff,
+                                                       ncell, bperm);
+        note_launch();
+    }
     const double* xs = g.xs.as<double>();
     const double Lz = g.box[2];
     const double rc = ctx->model.d.r_cut;
@@ -187,10 +262,10 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
         int32_t base = 0;
         P.n_le.assign(K + 1, 0);
         for (int m = 0; m <= K; ++m) {
-            k_flag_class<<<grid_for(n, 256), 256, 0, st>>>(cur, n, m, flag);
+            k_flag_class<<<grid_for(n, 256), 256, 0, st>>>(cur, bperm, n, m, flag);
             note_launch();
             MP_TRY(exclusive_scan_i32(flag, pre, n, ws.tmp, st));
-            k_place_class<<<grid_for(n, 256), 256, 0, st>>>(cur, pre, n, m, base,
+            k_place_class<<<grid_for(n, 256), 256, 0, st>>>(cur, bperm, pre, n, m, base,
                                                             P.gid.as<int32_t>(),
                                                             P.is_root.as<uint8_t>(), g2l);
             note_launch();
