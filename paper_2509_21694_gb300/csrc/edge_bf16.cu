@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                         hjc[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + jb + q * TF);
                     }
                 }
-#pragma unroll 1
+#pragma unroll 2
                 for (int i = 0; i < 8; ++i) {
                     const int e = sl * 8 + i;
                     const int lr = w.row[e];
