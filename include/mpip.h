@@ -172,7 +172,8 @@ typedef struct {
     int32_t n_layers;       /* K                                             */
     int32_t precision;      /* MP_FP32 / MP_BF16                             */
     int32_t n_parts;        /* partitions (1 = unpartitioned)                */
-    int32_t k_hops;         /* halo depth in hops / in units of r_c          */
+    int32_t k_hops;         /* halo depth in hops / in units of r_c; <= 0 =  */
+                            /* n_layers (the depth exactness needs)          */
     int32_t halo_mode;      /* MP_HALO_GEOM / MP_HALO_BFS                    */
     int32_t use_head;       /* add the correction head                       */
     int32_t forces_valid;   /* d_forces already holds F(d_pos)               */

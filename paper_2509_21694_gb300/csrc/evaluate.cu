@@ -44,15 +44,15 @@ __global__ void k_gather_local(const int32_t* __restrict__ gid, int64_t n,
     spl[l] = sp[s];
 }
 
+// h0 of layer 0 from the species embedding.  The l >= 1 features of layer 0
+// are zero and are not stored: every reader of layer 0 skips them.
 __global__ void k_embed(const int32_t* __restrict__ sp, int64_t n, int F, int NLM,
                         const float* __restrict__ emb, float* __restrict__ H) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t total = n * NLM * F;
-    if (idx >= total) return;
+    if (idx >= n * F) return;
     const int c = (int)(idx % F);
-    const int q = (int)((idx / F) % NLM);
-    const int64_t i = idx / ((int64_t)F * NLM);
-    H[idx] = q == 0 ? emb[(int64_t)sp[i] * F + c] : 0.f;
+    const int64_t i = idx / F;
+    H[i * NLM * F + c] = emb[(int64_t)sp[i] * F + c];
 }
 
 // Readout and adjoint seed: E_i = w_out . h0 + e0[z] (+ head), warp per atom.
@@ -276,7 +276,7 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         x = b.xl;
         sp = b.spl;
     }
-    k_embed<<<grid_for(feat, 256), 256, 0, st>>>(sp, n, F, NLM, m.emb, b.H);
+    k_embed<<<grid_for(n * F, 256), 256, 0, st>>>(sp, n, F, NLM, m.emb, b.H);
     note_launch();
     EdgeArgs ea{};
     ea.row_ptr = ss.row_ptr;
@@ -313,6 +313,7 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         na.Hin = b.H + t * feat;
         na.Hout = b.H + (t + 1) * feat;
         na.S = b.S + t * n * F;
+        na.first = t == 0;
         na.last = t == K - 1;
         {
             TimerScope ts(ctx, MP_TIMER_NODE_FWD, 0, rows);

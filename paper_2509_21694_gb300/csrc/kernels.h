@@ -44,6 +44,7 @@ struct NodeArgs {
     const float* Gout;   // adjoint
     float* Alpha;        // adjoint output (/N_avg)
     float inv_navg;
+    bool first;          // layer 0: input features with l >= 1 are zero (not stored)
     bool last;
     int* err;            // device error bits (tensor-core kernels)
 };

@@ -73,7 +73,9 @@ int md_run(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const dou
         MP_TRY(build_graph(ctx, d_pos, n, box, g));
         const Plan* pp = nullptr;
         if (o->n_parts > 1) {
-            MP_TRY(build_plan(ctx, g, o->n_parts, o->k_hops, o->halo_mode, plan, nullptr));
+            // the halo must reach K hops for the partitioned result to be exact
+            const int hops = o->k_hops > 0 ? o->k_hops : o->n_layers;
+            MP_TRY(build_plan(ctx, g, o->n_parts, hops, o->halo_mode, plan, nullptr));
             pp = &plan;
         }
         return evaluate(ctx, d_pos, d_species, g, pp, o->n_layers, o->precision, o->use_head, pe,

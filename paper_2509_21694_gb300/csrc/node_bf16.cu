@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_node_fwd_tc(NodeArgs a, LayerW wl, 
             const bool ok = i0 + r < a.n;
 #pragma unroll
             for (int q = 0; q < (LAST ? 1 : NLM9); ++q)
-                hin[q][r] = ok ? __ldg(a.Hin + ((i0 + r) * NLM9 + q) * NF + c) : 0.f;
+                hin[q][r] = (ok && (q == 0 || !a.first)) ? __ldg(a.Hin + ((i0 + r) * NLM9 + q) * NF + c) : 0.f;
         }
         float d[4];
         tc::tmem_ld4(tcol, d);

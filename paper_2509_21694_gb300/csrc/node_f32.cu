@@ -24,8 +24,8 @@ __global__ void __launch_bounds__(F) k_node_fwd(NodeArgs a, const float* __restr
                                                 const float* __restrict__ V1T,
                                                 const float* __restrict__ V2T) {
     constexpr int NLM = (LMAX + 1) * (LMAX + 1);
-    __shared__ float sA[TA][NLM][F];
-    __shared__ float sB[TA][LMAX][F];
+    __shared__ __align__(16) float sA[TA][NLM][F];
+    __shared__ __align__(16) float sB[TA][LMAX][F];
     const int d = threadIdx.x;
     const int64_t a0 = (int64_t)blockIdx.x * TA;
     const int na = (int)min((int64_t)TA, a.n - a0);
@@ -57,25 +57,44 @@ __global__ void __launch_bounds__(F) k_node_fwd(NodeArgs a, const float* __restr
 #pragma unroll
         for (int q = 0; q < NLM - 1; ++q) hv[t][q] = 0.f;
     }
-#pragma unroll 2
-    for (int c = 0; c < F; ++c) {
-        const float w0 = __ldg(&W0T[c * F + d]);
-        const float u1 = __ldg(&U1T[c * F + d]);
-        const float u2 = LMAX >= 2 ? __ldg(&U2T[c * F + d]) : 0.f;
-        const float v1 = LAST ? 0.f : __ldg(&V1T[c * F + d]);
-        const float v2 = (LAST || LMAX < 2) ? 0.f : __ldg(&V2T[c * F + d]);
+    // four input channels per step: the shared-memory reads are float4
+    for (int c4 = 0; c4 < F; c4 += 4) {
+        float w0[4], u1[4], u2[4], v1[4], v2[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = c4 + k;
+            w0[k] = __ldg(&W0T[c * F + d]);
+            u1[k] = __ldg(&U1T[c * F + d]);
+            u2[k] = LMAX >= 2 ? __ldg(&U2T[c * F + d]) : 0.f;
+            v1[k] = LAST ? 0.f : __ldg(&V1T[c * F + d]);
+            v2[k] = (LAST || LMAX < 2) ? 0.f : __ldg(&V2T[c * F + d]);
+        }
 #pragma unroll
         for (int t = 0; t < TA; ++t) {
-            float acc = fmaf(w0, sA[t][0][c], s[t]);
-            acc = fmaf(u1, sB[t][0][c], acc);
-            if (LMAX >= 2) acc = fmaf(u2, sB[t][1][c], acc);
+            const float4 a0v = *reinterpret_cast<const float4*>(&sA[t][0][c4]);
+            const float4 b1v = *reinterpret_cast<const float4*>(&sB[t][0][c4]);
+            float acc = s[t];
+            acc = fmaf(w0[0], a0v.x, acc); acc = fmaf(u1[0], b1v.x, acc);
+            acc = fmaf(w0[1], a0v.y, acc); acc = fmaf(u1[1], b1v.y, acc);
+            acc = fmaf(w0[2], a0v.z, acc); acc = fmaf(u1[2], b1v.z, acc);
+            acc = fmaf(w0[3], a0v.w, acc); acc = fmaf(u1[3], b1v.w, acc);
+            if (LMAX >= 2) {
+                const float4 b2v = *reinterpret_cast<const float4*>(&sB[t][1][c4]);
+                acc = fmaf(u2[0], b2v.x, acc); acc = fmaf(u2[1], b2v.y, acc);
+                acc = fmaf(u2[2], b2v.z, acc); acc = fmaf(u2[3], b2v.w, acc);
+            }
             s[t] = acc;
             if (!LAST) {
 #pragma unroll
-                for (int m = 1; m < 4; ++m) hv[t][m - 1] = fmaf(v1, sA[t][m][c], hv[t][m - 1]);
-                if (LMAX >= 2) {
-#pragma unroll
-                    for (int m = 4; m < 9; ++m) hv[t][m - 1] = fmaf(v2, sA[t][m][c], hv[t][m - 1]);
+                for (int q = 1; q < NLM; ++q) {
+                    const float4 av = *reinterpret_cast<const float4*>(&sA[t][q][c4]);
+                    const float* v = q < 4 ? v1 : v2;
+                    float h = hv[t][q - 1];
+                    h = fmaf(v[0], av.x, h);
+                    h = fmaf(v[1], av.y, h);
+                    h = fmaf(v[2], av.z, h);
+                    h = fmaf(v[3], av.w, h);
+                    hv[t][q - 1] = h;
                 }
             }
         }
@@ -88,7 +107,8 @@ __global__ void __launch_bounds__(F) k_node_fwd(NodeArgs a, const float* __restr
         a.Hout[base] = a.Hin[base] + silu(s[t]);
         if (!LAST) {
 #pragma unroll
-            for (int q = 1; q < NLM; ++q) a.Hout[base + q * F] = a.Hin[base + q * F] + hv[t][q - 1];
+            for (int q = 1; q < NLM; ++q)
+                a.Hout[base + q * F] = (a.first ? 0.f : a.Hin[base + q * F]) + hv[t][q - 1];
         }
     }
 }
