@@ -310,12 +310,15 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
             for (int sl = 0; sl < SCF / 16; ++sl) {
                 if (!wg_wait(w, phase, g)) { alive = false; break; }
                 // prefetch the first edge's sender features
-                float hjc[TNLM], hjn[TNLM];
+                float hjc[TNLM], hjn[TNLM], hjm[TNLM];
                 {
                     const int e0 = sl * 16;
                     const float* __restrict__ hp = Hin + ((int64_t)w.col[e0] * TNLM) * TF + c;
 #pragma unroll
                     for (int q = 0; q < TNLM; ++q) hjc[q] = (FIRST && q > 0) ? 0.f : __ldg(hp + q * TF);
+                    const float* __restrict__ hq = Hin + ((int64_t)w.col[e0 + 1] * TNLM) * TF + c;
+#pragma unroll
+                    for (int q = 0; q < TNLM; ++q) hjn[q] = (FIRST && q > 0) ? 0.f : __ldg(hq + q * TF);
                 }
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -325,10 +328,10 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
                     float R[PP::NP];
 #pragma unroll
                     for (int q = 0; q < PP::NP; ++q) tc::tmem_ld1(tl + 16 * q + i, R[q]);
-                    if (i + 1 < 16) {
-                        const float* __restrict__ hp = Hin + ((int64_t)w.col[e + 1] * TNLM) * TF + c;
+                    if (i + 2 < 16) {
+                        const float* __restrict__ hp = Hin + ((int64_t)w.col[e + 2] * TNLM) * TF + c;
 #pragma unroll
-                        for (int q = 0; q < TNLM; ++q) hjn[q] = (FIRST && q > 0) ? 0.f : __ldg(hp + q * TF);
+                        for (int q = 0; q < TNLM; ++q) hjm[q] = (FIRST && q > 0) ? 0.f : __ldg(hp + q * TF);
                     }
                     if (lr != cur) {
                         if (cur >= 0) {
@@ -357,7 +360,10 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
                         if (!FIRST) acc[4 + m] = fmaf(R[PP::slb(2)], hjc[4 + m], acc[4 + m]);
                     }
 #pragma unroll
-                    for (int q = 0; q < TNLM; ++q) hjc[q] = hjn[q];
+                    for (int q = 0; q < TNLM; ++q) {
+                        hjc[q] = hjn[q];
+                        hjn[q] = hjm[q];
+                    }
                 }
                 tc::fence_before_sync();
                 wg_sync(g);
