@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--layers", type=int, default=2)
     ap.add_argument("--parts", type=int, default=8)
     ap.add_argument("--cells", type=int, default=64, help="FCC cells per axis")
+    ap.add_argument("--structure", default="fcc", choices=["fcc", "liquid"],
+                    help="fcc: FCC Cu (cells^3 x 4 atoms); liquid: 3-species random liquid")
+    ap.add_argument("--atoms", type=int, default=32000, help="atoms of the liquid")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -60,19 +63,41 @@ def drift_slope(ledger, n_atoms, dt_fs):
     return float(np.polyfit(t, y, 1)[0])
 
 
+def system_and_model(args, cells=None, atoms=None):
+    """The benchmark structure (or a smaller block of the same kind) and model."""
+    import synth
+    if args.structure == "liquid":
+        # Cu/Ni/Al 0.5/0.3/0.2 at 0.08 A^-3, 1.8 A minimum distance; the pair
+        # term keeps the random packing from collapsing during the MD
+        s = synth.liquid3(n=atoms or args.atoms, seed=2)
+        d = synth.model_liquid(n_layers_full=6)
+        d.rep_eps = 0.3
+        w = synth.make_weights(d, 1)
+    else:
+        # thermal-scale random displacements (0.05 A) so the start is not a
+        # perfectly symmetric lattice
+        c = cells or args.cells
+        s = synth.cu_fcc_large(cells=(c,) * 3, sigma=0.05, seed=4)
+        d = synth.model_cu(n_layers_full=6)
+        w = synth.make_weights(d, 4)
+    return s, d, w
+
+
 def workload(args):
     import synth
-    # thermal-scale random displacements (0.05 A) so the start is not a
-    # perfectly symmetric lattice
-    s = synth.cu_fcc_large(cells=(args.cells,) * 3, sigma=0.05, seed=4)
-    d = synth.model_cu(n_layers_full=6)
-    w = synth.make_weights(d, 4)
+    s, d, w = system_and_model(args)
     v = synth.maxwell(s.masses, 600.0, 4)
     return s, d, w, v
 
 
+def n_atoms_of(args):
+    return args.atoms if args.structure == "liquid" else 4 * args.cells ** 3
+
+
 def config_dict(args, n_atoms):
-    return {"workload": "fcc-cu-%d-md-600K" % n_atoms, "atoms": n_atoms,
+    name = "liquid3-%d-md-600K" % n_atoms if args.structure == "liquid" else \
+        "fcc-cu-%d-md-600K" % n_atoms
+    return {"workload": name, "atoms": n_atoms,
             "layers_K": args.layers, "layers_full": 6, "F": 128, "lmax": 2, "r_cut_A": 6.0,
             "partitions": args.parts, "halo_A": 6.0 * args.layers, "halo_mode": "geometric",
             "dt_fs": 1.0, "precision": args.precision,
@@ -282,13 +307,11 @@ def run_ours(args, rank, world):
 # ------------------------------------------------------ oracle (CPU) --
 
 def oracle_sample_step(args, cells=6):
-    """One FP64 oracle MD step on a cells^3 block of the same lattice/model."""
-    import numpy as np
+    """One FP64 oracle MD step on a cells^3 block of the same lattice and
+    model (FCC), or an independently generated 864-atom cell of the liquid."""
     import synth
     from oracle import md as omd, model as om, neighbors as onb
-    s = synth.cu_fcc_large(cells=(cells,) * 3, sigma=0.0, seed=4)
-    d = synth.model_cu(n_layers_full=6)
-    w = synth.make_weights(d, 4)
+    s, d, w = system_and_model(args, cells=cells, atoms=4 * cells ** 3)
     v = synth.maxwell(s.masses, 600.0, 4)
 
     def force(p):
@@ -314,8 +337,13 @@ def cpu_baseline(args, cells=6, steps=1):
     dt = time.perf_counter() - t
     return {"value": n * steps / dt, "unit": UNIT, "cores": torch.get_num_threads(),
             "kind": "oracle",
-            "sample": "%d-atom FCC Cu block (%d^3 cells) of the same lattice and model, K=%d, "
-                      "%d MD step(s), FP64 torch CPU" % (n, cells, args.layers, steps)}
+            "sample": "%d-atom %s of the same kind and model, K=%d, %d MD step(s), FP64 "
+                      "torch CPU" % (n, sample_kind(args, cells), args.layers, steps)}
+
+
+def sample_kind(args, cells):
+    return ("liquid cell" if args.structure == "liquid"
+            else "FCC Cu block (%d^3 cells)" % cells)
 
 
 def run_reference(args):
@@ -330,12 +358,12 @@ def run_reference(args):
     dt = time.perf_counter() - t
     value = n * args.steps / dt
     cb = {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-          "sample": "%d-atom FCC Cu block of the same lattice and model per step, K=%d, FP64 "
-                    "torch CPU" % (n, args.layers)}
+          "sample": "%d-atom %s of the same kind and model per step, K=%d, FP64 torch "
+                    "CPU" % (n, sample_kind(args, 6), args.layers)}
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(args, 4 * args.cells ** 3),
+            "data": "synthetic", "config": config_dict(args, n_atoms_of(args)),
             "impl": "reference", "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
