@@ -52,6 +52,13 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM read + write bytes per edge of the tensor-core edge adjoint, averaged
+# over its layer-0 and layer-1 launches, from one ncu capture on 131,072 atoms
+# (profiles/edge_node_kernels_bf16_131k.md); scaled by the edges of a launch.
+# Must be re-measured whenever that kernel changes.
+TRAFFIC_BYTES_PER_EDGE_BF16 = {"bwd": 469.0}
+
+
 def drift_slope(ledger, n_atoms, dt_fs):
     """Least-squares slope of (E_tot(t) - E_tot(0)) / N over the timed steps,
     in meV/atom/ps."""
@@ -81,6 +88,16 @@ def system_and_model(args, cells=None, atoms=None):
         d = synth.model_cu(n_layers_full=6)
         w = synth.make_weights(d, 4)
     return s, d, w
+
+
+def kernel_ms(timing):
+    """CUDA-event milliseconds per kernel class; layer 0 of the edge kernels
+    is included in edge_fwd / edge_bwd and also listed on its own."""
+    out = {k: round(v["ms"], 3) for k, v in timing.items() if not k.endswith("_l0")}
+    for k in ("edge_fwd", "edge_bwd"):
+        out[k] = round(timing[k]["ms"] + timing[k + "_l0"]["ms"], 3)
+        out[k + "_layer0"] = round(timing[k + "_l0"]["ms"], 3)
+    return out
 
 
 def workload(args):
@@ -261,34 +278,43 @@ def run_ours(args, rank, world):
                "h2d_bytes_per_step": 2 * n * 3 * 8,
                "d2h_bytes_per_step": 2 * n * 3 * 8 + n * 3 * 4 + 3 * 8}
 
-    # roofline of the dominant kernel class
+    # roofline of the dominant kernel class (edge kernels: layer 0 and the
+    # later layers are timed separately and counted with their own FLOPs)
     peaks, peak_kind = load_peaks()
+    merged = {k: {"ms": timing[k]["ms"] + timing.get(k + "_l0", {"ms": 0.0})["ms"]}
+              for k in ("edge_fwd", "edge_bwd")}
     dom = max(("edge_fwd", "edge_bwd", "node_fwd", "node_bwd", "neighbors", "partition"),
-              key=lambda k: timing[k]["ms"])
+              key=lambda k: merged[k]["ms"] if k in merged else timing[k]["ms"])
     roof = None
-    t = timing[dom]
-    if dom in ("edge_fwd", "edge_bwd") and t["launches"]:
+    if dom in ("edge_fwd", "edge_bwd"):
         kind = "fwd" if dom == "edge_fwd" else "bwd"
-        # layer 0 launches process the first-layer form, the rest the full form
-        per_layer = t["edges"] / t["launches"]
-        flops_first = edge_flops(kind, 128, 2, True)
-        flops_rest = edge_flops(kind, 128, 2, False)
-        flops = per_layer * (flops_first + (args.layers - 1) * flops_rest) / args.layers
-        dur = t["ms"] / t["launches"] * 1e-3
-        achieved = flops / dur / 1e12
-        if args.precision == "fp32":
-            mhz = clk.get("sm_mhz") or 2070.0
-            peak = 152 * 128 * 2 * mhz * 1e6 / 1e12      # FP32 FFMA lanes x 2 FLOP x clock
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "k_edge_" + kind,
-                    "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x median SM clock %.0f MHz" % mhz,
-                    "flops_per_launch": flops}
-        else:
-            peak = peaks.get("bf16_tflops_sustained", 1700.0)
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "k_edge_" + kind,
-                    "peak_note": "bf16_tflops_sustained of %s peaks" % peak_kind,
-                    "flops_per_launch": flops}
+        t0, t1 = timing[dom + "_l0"], timing[dom]
+        launches_all = t0["launches"] + t1["launches"]
+        if launches_all:
+            flops = (t0["edges"] * edge_flops(kind, 128, 2, True) +
+                     t1["edges"] * edge_flops(kind, 128, 2, False)) / launches_all
+            dur = (t0["ms"] + t1["ms"]) / launches_all * 1e-3
+            achieved = flops / dur / 1e12
+            edges_per_launch = (t0["edges"] + t1["edges"]) / launches_all
+            if args.precision == "fp32":
+                mhz = clk.get("sm_mhz") or 2070.0
+                peak = 152 * 128 * 2 * mhz * 1e6 / 1e12      # FP32 FFMA lanes x 2 FLOP x clock
+                roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None, "kernel": "k_edge_" + kind,
+                        "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x median SM "
+                                     "clock %.0f MHz" % mhz,
+                        "flops_per_launch": flops}
+            else:
+                peak = peaks.get("bf16_tflops_sustained", 1700.0)
+                traffic = (TRAFFIC_BYTES_PER_EDGE_BF16[kind] * edges_per_launch
+                           if kind in TRAFFIC_BYTES_PER_EDGE_BF16 else None)
+                roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": traffic, "kernel": "k_edge_" + kind,
+                        "peak_note": "bf16_tflops_sustained of %s peaks" % peak_kind,
+                        "flops_per_launch": flops,
+                        "traffic_note": "DRAM bytes per edge from the ncu capture in "
+                                        "profiles/edge_node_kernels_bf16_131k.md x edges per "
+                                        "launch"}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -296,7 +322,7 @@ def run_ours(args, rank, world):
            "dtype": "bf16+fp32" if args.precision == "bf16" else "fp32", "data": "synthetic",
            "config": config_dict(args, n), "e2e": e2e, "gpu_launches": launches,
            "roofline": roof, "clocks": clk,
-           "kernel_ms": {k: round(v["ms"], 3) for k, v in timing.items()},
+           "kernel_ms": kernel_ms(timing),
            "energy_drift_meV_per_atom_ps": drift_slope(ledger, n, 1.0),
            "energy_drift_steps": int(ledger.shape[0]),
            "peaks": peak_kind}

@@ -225,11 +225,15 @@ int mp_head_get(mp_ctx* ctx, double* h_params, int64_t n);
  * library's kernels inside its own timed region. */
 #define MP_TIMER_NEIGHBORS   0   /* wrap, bin, cell sort, CSR count + fill     */
 #define MP_TIMER_PARTITION   1   /* root/halo flags, compaction, local CSR     */
-#define MP_TIMER_EDGE_FWD    2   /* edge forward (basis, radial MLP, messages) */
-#define MP_TIMER_EDGE_BWD    3   /* edge adjoint (forces, sender gradients)    */
+#define MP_TIMER_EDGE_FWD    2   /* edge forward (basis, radial MLP, messages), */
+                                 /* layers >= 1                                 */
+#define MP_TIMER_EDGE_BWD    3   /* edge adjoint (forces, sender gradients),    */
+                                 /* layers >= 1                                 */
 #define MP_TIMER_NODE_FWD    4   /* node update                                 */
 #define MP_TIMER_NODE_BWD    5   /* node adjoint                                */
-#define MP_TIMER_COUNT       6
+#define MP_TIMER_EDGE_FWD_L0 6   /* edge forward of layer 0 (l >= 1 inputs zero) */
+#define MP_TIMER_EDGE_BWD_L0 7   /* edge adjoint of layer 0                     */
+#define MP_TIMER_COUNT       8
 /* enable != 0 starts recording and clears the accumulators; 0 stops. */
 int mp_timing_enable(mp_ctx* ctx, int enable);
 /* Synchronises the stream, then fills host arrays of MP_TIMER_COUNT

@@ -301,7 +301,8 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         ea.Hin = b.H + t * feat;
         ea.Aout = b.A + t * feat;
         {
-            TimerScope ts(ctx, MP_TIMER_EDGE_FWD, pre.edges(K - 1 - t), rows);
+            TimerScope ts(ctx, t == 0 ? MP_TIMER_EDGE_FWD_L0 : MP_TIMER_EDGE_FWD,
+                          pre.edges(K - 1 - t), rows);
             if (precision == MP_BF16)
                 MP_TRY(launch_edge_fwd_bf16(m, ea, st, ctx->num_sms));
             else
@@ -378,7 +379,8 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         ea.Gin = t == 0 ? nullptr : Gin;
         ea.frc = b.floc;
         {
-            TimerScope ts(ctx, MP_TIMER_EDGE_BWD, pre.edges(K - t), erows);
+            TimerScope ts(ctx, t == 0 ? MP_TIMER_EDGE_BWD_L0 : MP_TIMER_EDGE_BWD, pre.edges(K - t),
+                          erows);
             if (precision == MP_BF16)
                 MP_TRY(launch_edge_bwd_bf16(m, ea, st, ctx->num_sms));
             else
