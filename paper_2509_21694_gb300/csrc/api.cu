@@ -93,7 +93,7 @@ static int upload_model(Model& m, const double* w) {
     auto takeh = [&](size_t k) { size_t o = nh; nh += (k + 63) / 64 * 64; return o; };
     size_t o_emb = takef((size_t)S * F), o_e0 = takef(S), o_wout = takef(F),
            o_head = takef((size_t)Hh * F + 2 * Hh + 1);
-    struct LO { size_t W1, W2, W2T, W3, W3T, W0, W0T, U[2], UT[2], b, V[2], VT[2]; size_t W2b, W3b, W3Tb, W2Tb, W2sw, W3sw, NswF; };
+    struct LO { size_t W1, W2, W2T, W3, W3T, W0, W0T, U[2], UT[2], b, V[2], VT[2]; size_t W2b, W3b, W3Tb, W2Tb, W2sw, W3sw, NswF, NswB; };
     const bool tc_shape = (F == 128 && lm == 2 && H == 64);
     std::vector<LO> lo(L);
     for (int t = 0; t < L; ++t) {
@@ -118,6 +118,7 @@ static int upload_model(Model& m, const double* w) {
         lo[t].W2sw = tc_shape ? takeh((size_t)128 * H) : 0;
         lo[t].W3sw = tc_shape ? takeh((size_t)P * H) : 0;
         lo[t].NswF = tc_shape ? takeh((size_t)5 * F * F) : 0;
+        lo[t].NswB = tc_shape ? takeh((size_t)5 * F * F) : 0;
     }
     std::vector<float> hf(nf, 0.f);
     std::vector<__nv_bfloat16> hh(nh > 0 ? nh : 1);
@@ -174,6 +175,7 @@ static int upload_model(Model& m, const double* w) {
                     for (int k = 0; k < F; ++k) {
                         const size_t blk = (size_t)(2 * g + k / 64) * 128 * 64;
                         put(lo[t].NswF + blk, r, k % 64, hf[mats[g] + (size_t)r * F + k]);
+                        put(lo[t].NswB + blk, r, k % 64, hf[mats[g] + (size_t)k * F + r]);
                     }
         }
     }
@@ -212,6 +214,7 @@ static int upload_model(Model& m, const double* w) {
         q.W2sw = tc_shape ? hbase + lo[t].W2sw : nullptr;
         q.W3sw = tc_shape ? hbase + lo[t].W3sw : nullptr;
         q.NswF = tc_shape ? hbase + lo[t].NswF : nullptr;
+        q.NswB = tc_shape ? hbase + lo[t].NswB : nullptr;
     }
     return MP_OK;
 }

@@ -62,9 +62,11 @@ struct LayerW {
     // W3 as (1 + 2 lmax) tiles of 128 rows (one per radial path).
     __nv_bfloat16* W2sw;
     __nv_bfloat16* W3sw;
-    // Node-update operand image (F = 128): [W0, U1, U2, V1, V2] (out, in),
-    // each two K-blocks of 64 in the same swizzled layout.
+    // Node-update operand images (F = 128): five 128 x 128 matrices, each two
+    // K-blocks of 64 in the same swizzled layout.  NswF = [W0, U1, U2, V1, V2]
+    // (out, in); NswB = their transposes (in, out) for the adjoint.
     __nv_bfloat16* NswF;
+    __nv_bfloat16* NswB;
 };
 
 struct Model {

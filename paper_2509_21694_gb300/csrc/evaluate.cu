@@ -364,7 +364,10 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         na.last = t == K - 1;
         {
             TimerScope ts(ctx, MP_TIMER_NODE_BWD, 0, nrows);
-            MP_TRY(launch_node_bwd_f32(m, na, st));   // FP32 in both precisions (linear adjoint)
+            if (precision == MP_BF16)
+                MP_TRY(launch_node_bwd_bf16(m, na, st, ctx->num_sms));
+            else
+                MP_TRY(launch_node_bwd_f32(m, na, st));
         }
         if (nrows < n)
             MP_CUDA_TRY(cudaMemsetAsync(b.alpha + nrows * row_f, 0,

@@ -50,8 +50,11 @@ struct NodeArgs {
 };
 int launch_node_fwd_f32(const Model& m, const NodeArgs& a, cudaStream_t st);
 int launch_node_bwd_f32(const Model& m, const NodeArgs& a, cudaStream_t st);
-// BF16 operands on tcgen05 (F = 128, lmax = 2), forward only.
+// BF16 operands on tcgen05 (F = 128, lmax = 2).  The adjoint splits its
+// per-partition operand into three BF16 parts, so it stays linear to FP32
+// rounding.
 int launch_node_fwd_bf16(const Model& m, const NodeArgs& a, cudaStream_t st, int num_sms);
+int launch_node_bwd_bf16(const Model& m, const NodeArgs& a, cudaStream_t st, int num_sms);
 
 // Tangent (forward-mode) pass of one layer along a displacement field v.
 struct TangentArgs {
