@@ -11,7 +11,10 @@
 // Atoms are re-ordered by cell (x fastest, z slowest) with a deterministic
 // counting sort; within a cell they keep increasing caller id.  Each row is
 // emitted by one warp scanning the stencil cells in increasing cell order,
-// so senders come out in increasing sorted id without a per-row sort.
+// so senders come out in increasing sorted id without a per-row sort.  The
+// default search runs one block per cell with the stencil's atoms staged in
+// shared memory; a warp-per-receiver search reading them from global memory
+// is the fallback for stencils too large to stage.
 #include "common.cuh"
 
 namespace mp {
@@ -19,6 +22,8 @@ namespace mp {
 namespace {
 
 constexpr int kErrOverlap = 1;
+constexpr int kErrCapacity = 2;    // a cell's stencil holds more than kCellCand atoms
+constexpr int kCellCand = 2048;    // candidates a cell block stages in shared memory
 
 __device__ __forceinline__ double wrap1(double x, double L) {
     double w = __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
@@ -190,6 +195,104 @@ __global__ void k_neighbors(const float4* __restrict__ xsf, const double* __rest
     if (!FILL && lane == 0) deg[s] = count;
 }
 
+// The same search with one block per cell: the cell's stencil atoms (the 27
+// cells, or all cells of an axis shorter than 3, in increasing cell order)
+// are staged once in shared memory, then each warp takes one of the cell's
+// receivers and scans them 32 at a time.  Candidate order, arithmetic and
+// therefore the CSR are identical to k_neighbors.  A cell whose stencil
+// exceeds kCellCand atoms sets kErrCapacity (the caller then falls back to
+// k_neighbors).
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_neighbors_cell(
+    const float4* __restrict__ xsf, const double* __restrict__ xs, BoxP b,
+    const int32_t* __restrict__ start, int32_t* __restrict__ deg,
+    const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col, int8_t* __restrict__ shift,
+    int* __restrict__ err) {
+    __shared__ float4 cpos[kCellCand];
+    __shared__ int32_t cidx[kCellCand];
+    __shared__ int rbeg[27], roff[28], s_nr;
+    const int cell = blockIdx.x;
+    const int sb = start[cell], se = start[cell + 1];
+    if (sb == se) return;
+    if (threadIdx.x == 0) {
+        const int cx = cell % b.nc[0], cy = (cell / b.nc[0]) % b.nc[1],
+                  cz = cell / (b.nc[0] * b.nc[1]);
+        int cs[3][3], ns[3];
+        ns[0] = stencil(cx, b.nc[0], cs[0]);
+        ns[1] = stencil(cy, b.nc[1], cs[1]);
+        ns[2] = stencil(cz, b.nc[2], cs[2]);
+        int nr = 0, tot = 0;
+        for (int iz = 0; iz < ns[2]; ++iz)
+            for (int iy = 0; iy < ns[1]; ++iy)
+                for (int ix = 0; ix < ns[0]; ++ix) {
+                    const int c = (cs[2][iz] * b.nc[1] + cs[1][iy]) * b.nc[0] + cs[0][ix];
+                    rbeg[nr] = start[c];
+                    roff[nr] = tot;
+                    tot += start[c + 1] - start[c];
+                    ++nr;
+                }
+        roff[nr] = tot;
+        s_nr = nr;
+    }
+    __syncthreads();
+    const int nr = s_nr, tot = roff[nr];
+    if (tot > kCellCand) {
+        if (threadIdx.x == 0) atomicOr(err, kErrCapacity);
+        return;
+    }
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+        int r = 0;
+        while (q >= roff[r + 1]) ++r;
+        const int k = rbeg[r] + (q - roff[r]);
+        cpos[q] = xsf[k];
+        cidx[q] = k;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int s = sb + warp; s < se; s += nw) {
+        const float4 pi = xsf[s];
+        const double xi[3] = {xs[3 * (int64_t)s], xs[3 * (int64_t)s + 1], xs[3 * (int64_t)s + 2]};
+        const int64_t out = FILL ? row_ptr[s] : 0;
+        int count = 0;
+        for (int kb = 0; kb < tot; kb += 32) {
+            const int q = kb + lane;
+            bool keep = false;
+            int code = 13, k = -1;
+            if (q < tot) {
+                k = cidx[q];
+                if (k != s) {
+                    const float4 pj = cpos[q];
+                    float d0 = pj.x - pi.x, d1 = pj.y - pi.y, d2 = pj.z - pi.z;
+                    float n0 = -rintf(d0 * b.invLf[0]), n1 = -rintf(d1 * b.invLf[1]),
+                          n2 = -rintf(d2 * b.invLf[2]);
+                    d0 = fmaf(n0, b.Lf[0], d0);
+                    d1 = fmaf(n1, b.Lf[1], d1);
+                    d2 = fmaf(n2, b.Lf[2], d2);
+                    float r2f = d0 * d0 + d1 * d1 + d2 * d2;
+                    if (r2f < b.rc2_lo) {
+                        keep = true;
+                        code = ((int)n0 + 1) * 9 + ((int)n1 + 1) * 3 + ((int)n2 + 1);
+                        if (r2f < 1e-6f) atomicOr(err, kErrOverlap);
+                    } else if (r2f <= b.rc2_hi) {
+                        double xj[3] = {xs[3 * (int64_t)k], xs[3 * (int64_t)k + 1],
+                                        xs[3 * (int64_t)k + 2]};
+                        double r2;
+                        keep = exact_pair(xi, xj, b, &code, &r2);
+                    }
+                }
+            }
+            unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (FILL && keep) {
+                int64_t e = out + count + __popc(m & ((1u << lane) - 1u));
+                col[e] = k;
+                shift[e] = (int8_t)code;
+            }
+            count += __popc(m);
+        }
+        if (!FILL && lane == 0) deg[s] = count;
+    }
+}
+
 __global__ void k_export(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                          const int8_t* __restrict__ shift, const int32_t* __restrict__ perm,
                          int64_t n, int32_t* __restrict__ recv, int32_t* __restrict__ send,
@@ -264,22 +367,38 @@ int build_graph(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3]
                                                       g.inv.as<int32_t>(), xs, xsf); note_launch();
     int warps_per_block = 8;
     int nb = grid_for(n, warps_per_block);
-    k_neighbors<false><<<nb, 32 * warps_per_block, 0, st>>>(
-        xsf, xs, n, b, g.cell_start.as<int32_t>(), deg, nullptr, nullptr, nullptr, err); note_launch();
+    // degrees with the cell-block search; a stencil too large for its shared
+    // memory switches both passes to the warp-per-receiver search
+    k_neighbors_cell<false><<<(unsigned)ncell, 256, 0, st>>>(
+        xsf, xs, b, g.cell_start.as<int32_t>(), deg, nullptr, nullptr, nullptr, err); note_launch();
+    int herr = 0;
+    MP_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaStreamSynchronize(st));
+    const bool by_cell = !(herr & kErrCapacity);
+    if (!by_cell) {
+        MP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+        k_neighbors<false><<<nb, 32 * warps_per_block, 0, st>>>(
+            xsf, xs, n, b, g.cell_start.as<int32_t>(), deg, nullptr, nullptr, nullptr, err); note_launch();
+    }
     MP_TRY(exclusive_scan_i64(deg, g.row_ptr.as<int64_t>(), n, ws.tmp, st));
     int64_t ne = 0;
     MP_CUDA_TRY(cudaMemcpyAsync(&ne, g.row_ptr.as<int64_t>() + n, sizeof(int64_t),
                                 cudaMemcpyDeviceToHost, st));
-    int herr = 0;
     MP_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));
     if (herr & kErrOverlap) return MP_ERR_OVERLAP;
     g.n_edges = ne;
     MP_TRY(g.col.reserve(sizeof(int32_t) * (ne + 1)));
     MP_TRY(g.shift.reserve(ne + 16));
-    k_neighbors<true><<<nb, 32 * warps_per_block, 0, st>>>(
-        xsf, xs, n, b, g.cell_start.as<int32_t>(), nullptr, g.row_ptr.as<int64_t>(),
-        g.col.as<int32_t>(), g.shift.as<int8_t>(), err); note_launch();
+    if (by_cell)
+        k_neighbors_cell<true><<<(unsigned)ncell, 256, 0, st>>>(
+            xsf, xs, b, g.cell_start.as<int32_t>(), nullptr, g.row_ptr.as<int64_t>(),
+            g.col.as<int32_t>(), g.shift.as<int8_t>(), err);
+    else
+        k_neighbors<true><<<nb, 32 * warps_per_block, 0, st>>>(
+            xsf, xs, n, b, g.cell_start.as<int32_t>(), nullptr, g.row_ptr.as<int64_t>(),
+            g.col.as<int32_t>(), g.shift.as<int8_t>(), err);
+    note_launch();
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }

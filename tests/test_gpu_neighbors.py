@@ -96,3 +96,15 @@ def test_error_codes(mp):
     with pytest.raises(mp.MPError) as e:
         mp.mp_build_neighbors(pot.ctx, pos, [20.0, 20.0, 20.0])
     assert e.value.code == -3
+
+
+def test_dense_stencil_fallback_bit_exact(mp):
+    # 2,500 atoms in a 12 A box with r_c = 5: 2 cells per axis, so every
+    # stencil holds all atoms, more than a cell block stages in shared
+    # memory; the warp-per-receiver search takes over and must agree too.
+    pos, box = synth.rsa_liquid(2500, 2500 / 12.0 ** 3, 0.6, 17)
+    pot = _pot(mp, 5.0)
+    ref = onb.edges(pos, box, 5.0)
+    got = _gpu_edges(mp, pot, pos, box)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
