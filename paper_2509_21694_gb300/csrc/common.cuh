@@ -120,7 +120,7 @@ struct SubSys {
 
 struct Workspace {
     DevBuf xl, sp, H, A, S, G0, G1, alpha, floc, eatom, esum, fsum, ebuf,
-        err, tmp, xw, perm_pos, pscr, red, headbuf, adam, sched,
+        err, tmp, xw, perm_pos, pscr, pstats, red, headbuf, adam, sched,
         corder;   // partition placement: cells in Morton order [ncell], sizes, offsets
 };
 

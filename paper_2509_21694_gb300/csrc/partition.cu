@@ -26,11 +26,24 @@ __device__ __forceinline__ int root_bin(double z, double L, int P) {
     return b < P - 1 ? b : P - 1;
 }
 
+// Rows of the extended set: n_ext = cnt[0] + ... + cnt[K] (on the device);
+// the grid covers all n atoms and rows l >= n_ext get degree 0.
+__device__ __forceinline__ int64_t ext_rows(const int32_t* cnt, int K) {
+    int64_t t = 0;
+    for (int m = 0; m <= K; ++m) t += cnt[m];
+    return t;
+}
+
 __global__ void k_local_deg(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                             const int32_t* __restrict__ gid, const int32_t* __restrict__ g2l,
-                            int64_t n_ext, int32_t* __restrict__ deg) {
+                            int64_t n, const int32_t* __restrict__ cnt, int K,
+                            int32_t* __restrict__ deg) {
     int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= n_ext) return;
+    if (l >= n) return;
+    if (l >= ext_rows(cnt, K)) {
+        deg[l] = 0;
+        return;
+    }
     int s = gid[l];
     int c = 0;
     for (int64_t e = row_ptr[s]; e < row_ptr[s + 1]; ++e) c += g2l[col[e]] >= 0;
@@ -39,11 +52,12 @@ __global__ void k_local_deg(const int64_t* __restrict__ row_ptr, const int32_t* 
 
 __global__ void k_local_fill(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                              const int8_t* __restrict__ shift, const int32_t* __restrict__ gid,
-                             const int32_t* __restrict__ g2l, int64_t n_ext,
+                             const int32_t* __restrict__ g2l, int64_t n,
+                             const int32_t* __restrict__ cnt, int K,
                              const int64_t* __restrict__ lrow, int32_t* __restrict__ lcol,
                              int8_t* __restrict__ lshift) {
     int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= n_ext) return;
+    if (l >= n || l >= ext_rows(cnt, K)) return;
     int s = gid[l];
     int64_t o = lrow[l];
     for (int64_t e = row_ptr[s]; e < row_ptr[s + 1]; ++e) {
@@ -136,18 +150,36 @@ __global__ void k_flag_class(const int32_t* __restrict__ cls, const int32_t* __r
 }
 
 // Place the atoms of class m after those of classes < m, in placement order.
+// pre = exclusive scan of the class-m flags (pre[n] = their count); the
+// counts of earlier classes are in cnt[0..m-1], and cnt[m] is recorded here.
 __global__ void k_place_class(const int32_t* __restrict__ cls, const int32_t* __restrict__ bperm,
-                              const int32_t* __restrict__ pre, int64_t n, int m, int32_t base,
-                              int32_t* __restrict__ gid, uint8_t* __restrict__ lroot,
-                              int32_t* __restrict__ g2l) {
+                              const int32_t* __restrict__ pre, int64_t n, int m,
+                              int32_t* __restrict__ cnt, int32_t* __restrict__ gid,
+                              uint8_t* __restrict__ lroot, int32_t* __restrict__ g2l) {
     int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= n) return;
+    if (pos == 0) cnt[m] = pre[n];
     const int s = bperm[pos];
     if (cls[s] != m) return;
+    int base = 0;
+    for (int q = 0; q < m; ++q) base += cnt[q];
     const int l = base + pre[pos];
     gid[l] = s;
     lroot[l] = m == 0 ? 1 : 0;
     g2l[s] = l;
+}
+
+// Per-partition sizes for the host: n_le[m] (rows of classes <= m), e_le[m]
+// (their edges), m = 0..K.
+__global__ void k_plan_stats(const int32_t* __restrict__ cnt, int K,
+                             const int64_t* __restrict__ lrow, int64_t* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t t = 0;
+    for (int m = 0; m <= K; ++m) {
+        t += cnt[m];
+        out[m] = t;
+        out[K + 1 + m] = lrow[t];
+    }
 }
 
 __global__ void k_plan_export(const int32_t* __restrict__ gid, const uint8_t* __restrict__ root,
@@ -234,9 +266,18 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
     const double* xs = g.xs.as<double>();
     const double Lz = g.box[2];
     const double rc = ctx->model.d.r_cut;
-    int64_t halo_total = 0;
+    // No host synchronisation until every partition is built: class counts
+    // stay on the device, buffers are sized by their upper bounds (n rows;
+    // a partition's edges are a subset of the graph's), and the sizes come
+    // back in one copy at the end.
+    DevBuf& stats = ws.pstats;
+    const int ns = 2 * (K + 1);
+    MP_TRY(stats.reserve(sizeof(int64_t) * n_parts * ns + sizeof(int32_t) * n_parts * (K + 1)));
+    int64_t* d_stats = stats.as<int64_t>();
+    int32_t* d_cnt = reinterpret_cast<int32_t*>(d_stats + (size_t)n_parts * ns);
     for (int p = 0; p < n_parts; ++p) {
         Part& P = plan.parts[p];
+        int32_t* cnt = d_cnt + (size_t)p * (K + 1);
         int32_t* cur = cls;
         if (mode == MP_HALO_GEOM) {
             k_class_geom<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, rc, K, cls);
@@ -254,53 +295,47 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
                 other = t;
             }
         }
-        // class counts, then a stable placement class by class
-        std::vector<int32_t> counts(K + 1);
+        // stable placement class by class
         MP_CUDA_TRY(cudaMemsetAsync(g2l, 0xFF, sizeof(int32_t) * n, st));
         MP_TRY(P.gid.reserve(sizeof(int32_t) * (n + 1)));
         MP_TRY(P.is_root.reserve(n + 16));
-        int32_t base = 0;
-        P.n_le.assign(K + 1, 0);
+        MP_TRY(P.row_ptr.reserve(sizeof(int64_t) * (n + 1)));
+        MP_TRY(P.col.reserve(sizeof(int32_t) * (g.n_edges + 1)));
+        MP_TRY(P.shift.reserve(g.n_edges + 16));
         for (int m = 0; m <= K; ++m) {
             k_flag_class<<<grid_for(n, 256), 256, 0, st>>>(cur, bperm, n, m, flag);
             note_launch();
             MP_TRY(exclusive_scan_i32(flag, pre, n, ws.tmp, st));
-            k_place_class<<<grid_for(n, 256), 256, 0, st>>>(cur, bperm, pre, n, m, base,
+            k_place_class<<<grid_for(n, 256), 256, 0, st>>>(cur, bperm, pre, n, m, cnt,
                                                             P.gid.as<int32_t>(),
                                                             P.is_root.as<uint8_t>(), g2l);
             note_launch();
-            int32_t cnt = 0;
-            MP_CUDA_TRY(cudaMemcpyAsync(&cnt, pre + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-            MP_CUDA_TRY(cudaStreamSynchronize(st));
-            counts[m] = cnt;
-            base += cnt;
-            P.n_le[m] = base;
         }
-        P.n_root = P.n_le[0];
-        P.n_ext = P.n_le[K];
-        MP_TRY(P.row_ptr.reserve(sizeof(int64_t) * (P.n_ext + 1)));
-        k_local_deg<<<grid_for(P.n_ext, 256), 256, 0, st>>>(
-            g.row_ptr.as<int64_t>(), g.col.as<int32_t>(), P.gid.as<int32_t>(), g2l, P.n_ext, flag);
+        k_local_deg<<<grid_for(n, 256), 256, 0, st>>>(
+            g.row_ptr.as<int64_t>(), g.col.as<int32_t>(), P.gid.as<int32_t>(), g2l, n, cnt, K, flag);
         note_launch();
-        MP_TRY(exclusive_scan_i64(flag, P.row_ptr.as<int64_t>(), P.n_ext, ws.tmp, st));
-        int64_t ne = 0;
-        MP_CUDA_TRY(cudaMemcpyAsync(&ne, P.row_ptr.as<int64_t>() + P.n_ext, sizeof(int64_t),
-                                    cudaMemcpyDeviceToHost, st));
-        MP_CUDA_TRY(cudaStreamSynchronize(st));
-        P.n_edges = ne;
-        MP_TRY(P.col.reserve(sizeof(int32_t) * (ne + 1)));
-        MP_TRY(P.shift.reserve(ne + 16));
-        k_local_fill<<<grid_for(P.n_ext, 256), 256, 0, st>>>(
+        MP_TRY(exclusive_scan_i64(flag, P.row_ptr.as<int64_t>(), n, ws.tmp, st));
+        k_local_fill<<<grid_for(n, 256), 256, 0, st>>>(
             g.row_ptr.as<int64_t>(), g.col.as<int32_t>(), g.shift.as<int8_t>(),
-            P.gid.as<int32_t>(), g2l, P.n_ext, P.row_ptr.as<int64_t>(), P.col.as<int32_t>(),
+            P.gid.as<int32_t>(), g2l, n, cnt, K, P.row_ptr.as<int64_t>(), P.col.as<int32_t>(),
             P.shift.as<int8_t>());
         note_launch();
-        // edge counts of the class prefixes (rows are in class order)
-        P.e_le.assign(K + 1, 0);
-        for (int m = 0; m <= K; ++m)
-            MP_CUDA_TRY(cudaMemcpyAsync(&P.e_le[m], P.row_ptr.as<int64_t>() + P.n_le[m],
-                                        sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        MP_CUDA_TRY(cudaStreamSynchronize(st));
+        k_plan_stats<<<1, 32, 0, st>>>(cnt, K, P.row_ptr.as<int64_t>(), d_stats + (size_t)p * ns);
+        note_launch();
+    }
+    std::vector<int64_t> h_stats((size_t)n_parts * ns);
+    MP_CUDA_TRY(cudaMemcpyAsync(h_stats.data(), d_stats, sizeof(int64_t) * h_stats.size(),
+                                cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaStreamSynchronize(st));
+    int64_t halo_total = 0;
+    for (int p = 0; p < n_parts; ++p) {
+        Part& P = plan.parts[p];
+        const int64_t* h = h_stats.data() + (size_t)p * ns;
+        P.n_le.assign(h, h + K + 1);
+        P.e_le.assign(h + K + 1, h + 2 * (K + 1));
+        P.n_root = P.n_le[0];
+        P.n_ext = P.n_le[K];
+        P.n_edges = P.e_le[K];
         halo_total += P.n_ext - P.n_root;
     }
     MP_CUDA_TRY(cudaGetLastError());

@@ -120,10 +120,14 @@ int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, DevBuf& tmp, 
 
 int DevBuf::reserve(size_t nbytes) {
     if (nbytes <= bytes && p) return MP_OK;
+    // a buffer that has to grow gets 1/8 of headroom, so sizes that drift
+    // from one MD step to the next (edge counts) do not reallocate each time
+    const bool grow = p != nullptr;
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
     size_t want = nbytes < 256 ? 256 : nbytes;
+    if (grow) want += want / 8;
     if (cudaMalloc(&p, want) != cudaSuccess) {
         cudaGetLastError();
         return MP_ERR_NOMEM;
