@@ -157,12 +157,15 @@ void mp_plan_free(mp_plan* plan);
  * graph (plan == NULL) or partition by partition with the adjoint seeded on
  * roots only and the results summed (Methods, "Global Output Integration").
  *   d_pos      [n][3] double, the positions g was built from.
- *   d_species  [n] int32 in 0..S-1.
+ *   d_species  [n] int32 in 0..S-1 (checked on the device: an index outside
+ *              the range is treated as 0 and the call returns MP_ERR_ARG).
  *   precision  MP_FP32 or MP_BF16.   use_head: add the correction head.
  *   d_energy   [1] double, written (FP64 sum of per-atom energies).
  *   d_forces   [n][3] float, written.
  *   d_e_atom   [n] double per-atom energies, or NULL.
- * Errors: MP_ERR_ARG, MP_ERR_UNSUPPORTED, MP_ERR_NOMEM, MP_ERR_CUDA. */
+ * Synchronises the stream once at the end (to read the device error word).
+ * Errors: MP_ERR_ARG, MP_ERR_UNSUPPORTED, MP_ERR_NOMEM, MP_ERR_CUDA,
+ * MP_ERR_TIMEOUT (a tensor-core kernel's bounded wait ran out). */
 int mp_energy_forces(mp_ctx* ctx, const double* d_pos, const int32_t* d_species,
                      const mp_graph* g, const mp_plan* plan, int n_layers, int precision,
                      int use_head, double* d_energy, float* d_forces, double* d_e_atom);

@@ -15,9 +15,12 @@ namespace mp {
 
 namespace {
 
+constexpr int kErrSpecies = 8;   // error word: a species index outside 0..S-1
+
 __global__ void k_gather_pos(const double* __restrict__ pos, const int32_t* __restrict__ species,
                              const int32_t* __restrict__ perm, int64_t n, double L0, double L1,
-                             double L2, double* __restrict__ xs, int32_t* __restrict__ sp) {
+                             double L2, int n_species, double* __restrict__ xs,
+                             int32_t* __restrict__ sp, int* __restrict__ err) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int64_t i = perm[s];
@@ -29,7 +32,12 @@ __global__ void k_gather_pos(const double* __restrict__ pos, const int32_t* __re
         if (w >= L[a]) w = __dsub_rn(w, L[a]);
         xs[3 * s + a] = w;
     }
-    sp[s] = species[i];
+    int z = species[i];
+    if (z < 0 || z >= n_species) {   // reported after the evaluation; never indexes out of range
+        atomicOr(err, kErrSpecies);
+        z = 0;
+    }
+    sp[s] = z;
 }
 
 __global__ void k_gather_local(const int32_t* __restrict__ gid, int64_t n,
@@ -464,7 +472,8 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
     b.eloc = ws.eatom.as<double>();
 
     k_gather_pos<<<grid_for(n, 256), 256, 0, st>>>(d_pos, d_species, g.perm.as<int32_t>(), n,
-                                                   g.box[0], g.box[1], g.box[2], b.xs, b.sp); note_launch();
+                                                   g.box[0], g.box[1], g.box[2], m.d.n_species,
+                                                   b.xs, b.sp, ws.err.as<int>()); note_launch();
     MP_CUDA_TRY(cudaMemsetAsync(b.f_sorted, 0, sizeof(double) * 3 * n, st));
     MP_CUDA_TRY(cudaMemsetAsync(b.e_sorted, 0, sizeof(double) * n, st));
     const EdgeConst kc = make_edge_const(m.d, g.box);
@@ -473,13 +482,12 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
                                                  d_forces, d_e_atom); note_launch();
     MP_TRY(reduce_sum(b.e_sorted, n, d_energy, ws.red, st));
     MP_CUDA_TRY(cudaGetLastError());
-    if (precision == MP_BF16 && K > 0) {
-        // tensor-core kernels report bounded-wait timeouts in the error word
-        int herr = 0;
-        MP_CUDA_TRY(cudaMemcpyAsync(&herr, ws.err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
-        MP_CUDA_TRY(cudaStreamSynchronize(st));
-        if (herr) return MP_ERR_TIMEOUT;
-    }
+    // error word: invalid species; bounded-wait timeouts of the tensor-core kernels
+    int herr = 0;
+    MP_CUDA_TRY(cudaMemcpyAsync(&herr, ws.err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr & kErrSpecies) return MP_ERR_ARG;
+    if (herr) return MP_ERR_TIMEOUT;
     return MP_OK;
 }
 

@@ -124,3 +124,21 @@ def test_deterministic_repeat(mp):
     a = _gpu(mp, d, w, s, 2)
     b = _gpu(mp, d, w, s, 2)
     assert a[0] == b[0] and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_invalid_species_is_an_argument_error(mp, precision):
+    # A species index outside 0..S-1 is caught on the device (treated as 0,
+    # reported after the evaluation); the context stays usable.
+    s = synth.alloy_fcc(cells=(4, 4, 4), sigma=0.05, seed=3)
+    d = synth.model_alloy(n_layers_full=2)
+    pot = mp.Potential(d, synth.make_weights(d, 1))
+    pos = torch.tensor(s.pos, device="cuda")
+    bad = torch.tensor(s.species, device="cuda")
+    bad[17] = d.n_species
+    with pytest.raises(mp.MPError) as e:
+        pot.energy_forces(pos, bad, s.box, 2, precision)
+    assert e.value.code == -1
+    E, F, _ = pot.energy_forces(pos, torch.tensor(s.species, device="cuda"), s.box, 2, precision)
+    assert torch.isfinite(F).all() and np.isfinite(E.item())
+    pot.close()
