@@ -59,6 +59,22 @@ def parse():
 TRAFFIC_BYTES_PER_EDGE_BF16 = {"bwd": 469.0}
 
 
+def max_over_ranks(ms, world, dev):
+    """The slowest rank's time: every rank runs its own copy of the workload
+    (no data-path collective), the job is done when the last one is."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world, n_atoms, steps, ms_max):
+    """Whole-job atom-steps/s: all ranks' atom-steps over the slowest time."""
+    return world * n_atoms * steps / (ms_max * 1e-3)
+
+
 def drift_slope(ledger, n_atoms, dt_fs):
     """Least-squares slope of (E_tot(t) - E_tot(0)) / N over the timed steps,
     in meV/atom/ps."""
@@ -238,13 +254,8 @@ def run_ours(args, rank, world):
     launches = mp.mp_kernel_launches() - launches0
     timing = mp.mp_timing_read(ctx)
     mp.mp_timing_enable(ctx, False)
-    ms = t0.elapsed_time(t1)
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * n * args.steps / (ms_max * 1e-3)
+    ms_max = max_over_ranks(t0.elapsed_time(t1), world, dev)
+    value = weak_value(world, n, args.steps, ms_max)
 
     # end-to-end through the C ABI from pinned host buffers: every step copies
     # positions and velocities in, runs one MD step and reads back positions,
@@ -269,12 +280,8 @@ def run_ours(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ems = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * n * args.steps / (ems * 1e-3), "unit": UNIT,
+        ems = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        e2e = {"value": weak_value(world, n, args.steps, ems), "unit": UNIT,
                "h2d_bytes_per_step": 2 * n * 3 * 8,
                "d2h_bytes_per_step": 2 * n * 3 * 8 + n * 3 * 4 + 3 * 8}
 
