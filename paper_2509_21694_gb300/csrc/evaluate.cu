@@ -336,25 +336,27 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
                                         sizeof(float) * (n - rows) * row_f, st));
     }
     // Readout on roots; adjoint seeds of every other atom are zero.
-    const int64_t n_roots = pre.rows(0);
-    {
+    const int64_t n_roots = pre.rows(0);   // may be 0: a slab without atoms
+    if (n_roots > 0) {
         const int wpb = 4;
         k_readout<<<grid_for(n_roots, wpb), 32 * wpb, sizeof(float) * F * wpb, st>>>(
             n_roots, F, NLM, b.H + (int64_t)K * feat, sp, m.w_out, m.e0,
             use_head ? m.head : nullptr, ss.is_root, b.eloc, b.G[K & 1]);
         note_launch();
-        if (n_roots < n)
-            MP_CUDA_TRY(cudaMemsetAsync(b.G[K & 1] + n_roots * row_f, 0,
-                                        sizeof(float) * (n - n_roots) * row_f, st));
     }
+    if (n_roots < n)
+        MP_CUDA_TRY(cudaMemsetAsync(b.G[K & 1] + n_roots * row_f, 0,
+                                    sizeof(float) * (n - n_roots) * row_f, st));
     MP_CUDA_TRY(cudaMemsetAsync(b.floc, 0, sizeof(double) * 3 * n, st));
     if (m.d.rep_eps != 0.0) {
         const int wpb = 8;
         // atoms beyond one hop of a root have no root neighbour: zero force
         const int64_t n_pair = pre.rows(1);
-        k_pair_term<<<grid_for(n_pair, wpb), 32 * wpb, 0, st>>>(n_pair, ss.row_ptr, ss.col, ss.shift, x, kc,
-                                                           ss.is_root, b.eloc, b.floc);
-        note_launch();
+        if (n_pair > 0) {
+            k_pair_term<<<grid_for(n_pair, wpb), 32 * wpb, 0, st>>>(
+                n_pair, ss.row_ptr, ss.col, ss.shift, x, kc, ss.is_root, b.eloc, b.floc);
+            note_launch();
+        }
     }
     // Adjoint: alpha of layer t is nonzero only within K-1-t hops (node pass
     // there, zero beyond); the edge pass covers rows within K-t hops, and the
@@ -430,9 +432,11 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
                               g.shift.as<int8_t>(), nullptr, nullptr, {}, {}});
     } else {
         for (const Part& P : plan->parts)
-            subs.push_back(SubSys{P.n_ext, P.n_edges, P.row_ptr.as<int64_t>(), P.col.as<int32_t>(),
-                                  P.shift.as<int8_t>(), P.gid.as<int32_t>(),
-                                  P.is_root.as<uint8_t>(), P.n_le, P.e_le});
+            if (P.n_root > 0)   // a slab without roots contributes nothing
+                subs.push_back(SubSys{P.n_ext, P.n_edges, P.row_ptr.as<int64_t>(),
+                                      P.col.as<int32_t>(), P.shift.as<int8_t>(),
+                                      P.gid.as<int32_t>(), P.is_root.as<uint8_t>(), P.n_le,
+                                      P.e_le});
     }
     int64_t nmax = 0;
     for (const SubSys& s : subs) nmax = s.n > nmax ? s.n : nmax;

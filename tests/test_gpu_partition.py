@@ -85,3 +85,31 @@ def test_truncated_halo_is_detected(mp):
     F0 = F0.cpu().numpy()
     assert np.abs(F1.cpu().numpy() - F0).max() > 1e-4 * np.sqrt((F0 ** 2).mean())
     pot.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_slabs_without_roots(mp, precision):
+    # 128 slabs of 0.45 A on a 57.6 A cell whose (001) atom planes are 1.8 A
+    # apart (displacements 0.05 A): about half the slabs hold no atom.  They
+    # must contribute nothing, and the rest must still equal the
+    # unpartitioned run.
+    s = synth.alloy_fcc(cells=(4, 4, 16), sigma=0.05, seed=12)
+    d = synth.model_alloy(n_layers_full=2)
+    d.rep_eps = 0.3
+    w = synth.make_weights(d, 1)
+    pot, pos, sp = _setup(mp, s, d, w)
+    g = mp.mp_build_neighbors(pot.ctx, pos, s.box)
+    plan, _ = mp.mp_partition(pot.ctx, g, 128, 2, 0)
+    try:
+        roots = [mp.mp_plan_info(plan, p)[1] for p in range(128)]
+    finally:
+        mp.mp_plan_free(plan)
+        mp.mp_graph_free(g)
+    assert min(roots) == 0 and sum(roots) == len(s.pos)
+    E0, F0, e0 = pot.energy_forces(pos, sp, s.box, 2, precision, per_atom=True)
+    E1, F1, e1 = pot.energy_forces(pos, sp, s.box, 2, precision, n_parts=128, per_atom=True)
+    F0 = F0.cpu().numpy().astype(np.float64)
+    F1 = F1.cpu().numpy().astype(np.float64)
+    assert np.abs(F1 - F0).max() <= 1e-6 * np.sqrt((F0 ** 2).mean())
+    assert np.array_equal(e0.cpu().numpy(), e1.cpu().numpy())
+    pot.close()
