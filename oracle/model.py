@@ -29,11 +29,16 @@ initial state and readout
 pruning: a K-layer evaluation uses layers 1..K of the L_full weight set and
 the same readout.
 
+stress (energy_forces_stress)
+  sigma = (1/V) dE/d(eps) for the homogeneous strain d_e -> (I + eps) d_e
+
 Parity pins (tests/test_oracle_*.py): Bessel and envelope closed forms and
 envelope derivatives at x = 1, spherical-harmonic norms, parity and addition
 theorem, the analytic dimer energy curve, K = 0 special case, translation /
 rotation / permutation invariance, perfect-FCC zero forces, supercell
-replication, sum F = 0 and central finite differences of the energy.
+replication, sum F = 0 and central finite differences of the energy; for the
+stress: central differences over real rescalings of the cell, the closed-form
+pair-potential virial, symmetry, and the partition sum.
 """
 from __future__ import annotations
 
@@ -83,9 +88,13 @@ def _t(a):
 
 
 def atom_energies(pos_t, species, box, recv, send, code, w, desc, n_layers,
-                  use_head=False, collect=None):
+                  use_head=False, collect=None, strain=None):
     """Per-atom energies E_i (torch float64 [N]) as a differentiable function
-    of pos_t; recv/send/code is the edge list of these positions."""
+    of pos_t; recv/send/code is the edge list of these positions.  With
+    ``strain`` (a 3 x 3 tensor eps) every edge vector is deformed as
+    d -> (I + eps) d, which is what a homogeneous strain of positions and box
+    does to it (the edge set itself does not change under an infinitesimal
+    strain)."""
     F, lmax = desc.F, desc.lmax
     N = pos_t.shape[0]
     recv_t = torch.as_tensor(recv, dtype=torch.long)
@@ -94,6 +103,8 @@ def atom_energies(pos_t, species, box, recv, send, code, w, desc, n_layers,
     species_t = torch.as_tensor(species, dtype=torch.long)
 
     d = pos_t[send_t] - pos_t[recv_t] + shift
+    if strain is not None:
+        d = d @ (torch.eye(3, dtype=_T) + strain).T
     r = torch.sqrt((d * d).sum(1))
     x = r / desc.r_cut
     env = envelope(x, desc.p_env)
@@ -160,6 +171,33 @@ def energy_forces(pos, species, box, edges, w, desc, n_layers, seed_mask=None,
         return float(E), Ei.detach().numpy(), np.zeros_like(pos_w)
     (g,) = torch.autograd.grad(E, pos_t)
     return float(E.detach()), Ei.detach().numpy(), -g.numpy()
+
+
+def energy_forces_stress(pos, species, box, edges, w, desc, n_layers, seed_mask=None,
+                         use_head=False):
+    """(E, E_i, F, sigma) in float64 numpy.
+
+    sigma = (1 / V) dE/d(eps) at eps = 0 (3 x 3, eV / A^3): the derivative of
+    the energy with respect to a homogeneous strain of positions and box,
+    taken by reverse-mode autograd through the deformed edge vectors
+    (Methods, "Global Output Integration": stress decomposes over the
+    per-atom energies like the forces).  E, E_i, F as in energy_forces.
+    """
+    box = np.asarray(box, dtype=np.float64)
+    pos_w = wrap(np.asarray(pos, dtype=np.float64), box)
+    pos_t = torch.tensor(pos_w, dtype=_T, requires_grad=True)
+    eps = torch.zeros(3, 3, dtype=_T, requires_grad=True)
+    recv, send, code = edges
+    Ei = atom_energies(pos_t, species, box, recv, send, code, w, desc, n_layers,
+                       use_head=use_head, strain=eps)
+    E = Ei.sum() if seed_mask is None else (Ei * _t(seed_mask)).sum()
+    vol = float(np.prod(box))
+    if not E.requires_grad:
+        return float(E), Ei.detach().numpy(), np.zeros_like(pos_w), np.zeros((3, 3))
+    gp, ge = torch.autograd.grad(E, [pos_t, eps], allow_unused=True)
+    F = np.zeros_like(pos_w) if gp is None else -gp.numpy()
+    sig = np.zeros((3, 3)) if ge is None else ge.numpy() / vol
+    return float(E.detach()), Ei.detach().numpy(), F, sig
 
 
 def energy(pos, species, box, edges, w, desc, n_layers, use_head=False):
