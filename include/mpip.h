@@ -170,6 +170,22 @@ int mp_energy_forces(mp_ctx* ctx, const double* d_pos, const int32_t* d_species,
                      const mp_graph* g, const mp_plan* plan, int n_layers, int precision,
                      int use_head, double* d_energy, float* d_forces, double* d_e_atom);
 
+/* As mp_energy_forces, plus the stress of the potential energy (Methods,
+ * "Global Output Integration": stress is assembled from the partitions like
+ * the forces).
+ *   d_stress  [3][3] double (device, row-major), written:
+ *             sigma = (1/V) dE/d(eps), the derivative of E under the
+ *             homogeneous strain r -> (I + eps) r of positions and box, in
+ *             eV/A^3; V = box volume.  Computed as the virial
+ *             1/(2V) sum over rows and their edges of g_e (x) d_e, with g_e
+ *             the pair gradient the adjoint adds to the row's force and d_e
+ *             the edge vector (each pair is visited from both ends).
+ * Errors: as mp_energy_forces; MP_ERR_ARG if d_stress is NULL. */
+int mp_energy_forces_stress(mp_ctx* ctx, const double* d_pos, const int32_t* d_species,
+                            const mp_graph* g, const mp_plan* plan, int n_layers, int precision,
+                            int use_head, double* d_energy, float* d_forces, double* d_e_atom,
+                            double* d_stress);
+
 /* ---- molecular dynamics ------------------------------------------------ */
 typedef struct {
     int32_t n_layers;       /* K                                             */

@@ -71,6 +71,7 @@ def _load():
         "mp_plan_export": (I32, [P, I32, P, P]),
         "mp_plan_free": (None, [P]),
         "mp_energy_forces": (I32, [P, P, P, P, P, I32, I32, I32, P, P, P]),
+        "mp_energy_forces_stress": (I32, [P, P, P, P, P, I32, I32, I32, P, P, P, P]),
         "mp_md_step": (I32, [P, P, P, P, P, P, I64, ctypes.POINTER(D), D, I32,
                              ctypes.POINTER(mp_md_opts), P]),
         "mp_kernel_launches": (I32, [ctypes.POINTER(I64)]),
@@ -239,6 +240,20 @@ def mp_energy_forces(ctx: int, pos: torch.Tensor, species: torch.Tensor, g: int,
     return energy, forces, e_atom
 
 
+def mp_energy_forces_stress(ctx: int, pos: torch.Tensor, species: torch.Tensor, g: int, plan,
+                            n_layers: int, precision: int = MP_FP32, use_head: bool = False,
+                            e_atom: torch.Tensor | None = None):
+    """(E, F, e_atom, stress[3, 3]) with stress = (1/V) dE/d(strain) in eV/A^3."""
+    n = pos.shape[0]
+    energy = torch.empty(1, dtype=torch.float64, device=pos.device)
+    forces = torch.empty(n, 3, dtype=torch.float32, device=pos.device)
+    stress = torch.empty(3, 3, dtype=torch.float64, device=pos.device)
+    _check(_lib.mp_energy_forces_stress(ctx, _ptr(pos), _ptr(species), g, plan or None, n_layers,
+                                        precision, int(use_head), _ptr(energy), _ptr(forces),
+                                        _ptr(e_atom), _ptr(stress)), "mp_energy_forces_stress")
+    return energy, forces, e_atom, stress
+
+
 def mp_md_step(ctx: int, pos, vel, forces, mass, species, box, dt: float, n_steps: int,
                n_layers: int, precision: int = MP_FP32, n_parts: int = 1, k_hops: int = 0,
                halo_mode: int = MP_HALO_GEOM, use_head: bool = False, forces_valid: bool = False,
@@ -360,6 +375,24 @@ class Potential:
                 mp_plan_free(plan)
             mp_graph_free(g)
         return E, F, e_atom
+
+    def energy_forces_stress(self, pos, species, box, n_layers, precision=MP_FP32, n_parts=1,
+                             k_hops=None, halo_mode=MP_HALO_GEOM, use_head=False):
+        """As energy_forces, plus the 3 x 3 stress (eV/A^3)."""
+        mp_set_stream(self.ctx, _stream())
+        g = mp_build_neighbors(self.ctx, pos, box)
+        plan = None
+        try:
+            if n_parts > 1:
+                plan, _ = mp_partition(self.ctx, g, n_parts,
+                                       n_layers if k_hops is None else k_hops, halo_mode)
+            E, F, _, S = mp_energy_forces_stress(self.ctx, pos, species, g, plan, n_layers,
+                                                 precision, use_head)
+        finally:
+            if plan:
+                mp_plan_free(plan)
+            mp_graph_free(g)
+        return E, F, S
 
 
 class EnergyForces(torch.autograd.Function):

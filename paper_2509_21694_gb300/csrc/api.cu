@@ -385,6 +385,16 @@ int mp_energy_forces(mp_ctx* ctx, const double* d_pos, const int32_t* d_species,
                     use_head, d_energy, d_forces, d_e_atom);
 }
 
+int mp_energy_forces_stress(mp_ctx* ctx, const double* d_pos, const int32_t* d_species,
+                            const mp_graph* g, const mp_plan* plan, int n_layers, int precision,
+                            int use_head, double* d_energy, float* d_forces, double* d_e_atom,
+                            double* d_stress) {
+    if (!ctx || !g || !d_stress) return MP_ERR_ARG;
+    if (plan && plan->ctx != ctx) return MP_ERR_ARG;
+    return evaluate(ctx, d_pos, d_species, g->g, plan ? &plan->p : nullptr, n_layers, precision,
+                    use_head, d_energy, d_forces, d_e_atom, d_stress);
+}
+
 int mp_md_step(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const double* d_mass,
                const int32_t* d_species, int64_t n, const double box[3], double dt_fs,
                int n_steps, const mp_md_opts* opts, double* h_ledger) {

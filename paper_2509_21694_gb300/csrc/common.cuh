@@ -120,7 +120,7 @@ struct SubSys {
 
 struct Workspace {
     DevBuf xl, sp, H, A, S, G0, G1, alpha, floc, eatom, esum, fsum, ebuf,
-        err, tmp, xw, perm_pos, pscr, pstats, red, headbuf, adam, sched,
+        err, tmp, xw, perm_pos, pscr, pstats, red, headbuf, adam, sched, vir,
         corder;   // partition placement: cells in Morton order [ncell], sizes, offsets
 };
 
@@ -175,7 +175,7 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
 // evaluate.cu
 int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,
              const Plan* plan, int n_layers, int precision, int use_head, double* d_energy,
-             float* d_forces, double* d_e_atom);
+             float* d_forces, double* d_e_atom, double* d_stress = nullptr);
 // head.cu
 int64_t head_param_count(const Model& m);
 int head_loss_grad(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,

@@ -84,6 +84,7 @@ struct alignas(1024) WgState {
     float u[SCB][4];                 // unit vector, r
     int row[SCF], col[SCF];
     double fpart[RPG][4][3];         // per-row, per-warp force partial sums
+    double vpart[RPG][4][9];         // per-row, per-warp virial partial sums (stress)
     int64_t rp[RPG + 1];
     int64_t next_grp;                // next row group, fetched by the leader
     uint64_t mbar;
@@ -96,6 +97,7 @@ struct SmemTC {
     WgState wg[NWG];
     uint32_t taddr;
 };
+static_assert(sizeof(SmemTC) + 1024 <= 232448, "shared memory of the edge kernels");
 
 __device__ __forceinline__ SmemTC& smem_tc(unsigned char* raw) {
     uintptr_t p = (reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023);
@@ -397,7 +399,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // Adjoint tile rows: row 2 e holds edge e, row 2 e + 1 its r-tangent, so a
 // 16-row slice is 8 edges and D2 columns (2 i, 2 i + 1) are (R, dR/dr).
-template <bool FIRST>
+template <bool FIRST, bool STRESS>
 __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, int64_t n_groups,
                                                         int* err) {
     using PP = TPaths<FIRST>;
@@ -422,12 +424,19 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
         const int nrows = (int)min((int64_t)RPG_B, a.n - r0);
         if (lt <= nrows) w.rp[lt] = a.row_ptr[r0 + lt];
         for (int q = lt; q < RPG_B * 12; q += 128) (&w.fpart[0][0][0])[q] = 0.0;
+        if (STRESS)
+            for (int q = lt; q < RPG_B * 36; q += 128) (&w.vpart[0][0][0])[q] = 0.0;
         wg_sync(g);
         const int64_t e_beg = w.rp[0], e_end = w.rp[nrows];
         float gacc[TNLM], ak[TNLM], hk[TNLM];
         // this channel's share of the row force: FP32 partial sums over a slice
         // (fs), folded into a compensated row sum (fk, fc) once per slice
         float fk[3] = {0.f, 0.f, 0.f}, fc[3] = {0.f, 0.f, 0.f}, fs[3] = {0.f, 0.f, 0.f};
+        // with STRESS: this channel's share of the row's virial sum_e g_e (x) d_e
+        // (a global sum, so plain FP32 per row suffices)
+        float va[STRESS ? 9 : 1];
+#pragma unroll
+        for (int q = 0; q < (STRESS ? 9 : 1); ++q) va[q] = 0.f;
         auto fold = [&]() {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -453,6 +462,13 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                 for (int q = 0; q < 3; ++q) {
                     const double v = warp_sum_d((double)fk[q] - (double)fc[q]);
                     if (lane == 0) w.fpart[lr][warp & 3][q] = v;
+                }
+                if (STRESS) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        const double v = warp_sum_d((double)va[q]);
+                        if (lane == 0) w.vpart[lr][warp & 3][q] = v;
+                    }
                 }
             }
         };
@@ -592,6 +608,10 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                         }
 #pragma unroll
                         for (int q = 0; q < 3; ++q) fk[q] = fc[q] = 0.f;
+                        if (STRESS) {
+#pragma unroll
+                            for (int q = 0; q < 9; ++q) va[q] = 0.f;
+                        }
                     }
                     tc::tmem_wait_ld();
                     float Y[TNLM];
@@ -658,8 +678,22 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                     float v[3];
                     sph_grad<TLMAX, float>(u, gy, v);
                     const float vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
+                    if (STRESS) {
+                        float gq[3];
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) fs[q] += fmaf(gr, u[q], (v[q] - vu * u[q]) * ir);
+                        for (int q = 0; q < 3; ++q) {
+                            gq[q] = fmaf(gr, u[q], (v[q] - vu * u[q]) * ir);
+                            fs[q] += gq[q];
+                        }
+                        const float r = 1.f / ir;
+#pragma unroll
+                        for (int p = 0; p < 3; ++p)
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) va[3 * p + q] = fmaf(gq[p], u[q] * r, va[3 * p + q]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) fs[q] += fmaf(gr, u[q], (v[q] - vu * u[q]) * ir);
+                    }
 #pragma unroll
                     for (int q = 0; q < TNLM; ++q) {
                         ajc[q] = ajn[q];
@@ -689,6 +723,11 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
             const int lr = lt / 3, q = lt % 3;
             const double f = w.fpart[lr][0][q] + w.fpart[lr][1][q] + w.fpart[lr][2][q] + w.fpart[lr][3][q];
             a.frc[(r0 + lr) * 3 + q] += f;
+        }
+        if (STRESS && lt < nrows * 9) {
+            const int lr = lt / 9, q = lt % 9;
+            const double v = w.vpart[lr][0][q] + w.vpart[lr][1][q] + w.vpart[lr][2][q] + w.vpart[lr][3][q];
+            a.vir[(int64_t)q * a.vir_stride + r0 + lr] += v;
         }
         wg_sync(g);
     }
@@ -723,8 +762,11 @@ int launch_edge_fwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int
 int launch_edge_bwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int num_sms) {
     if (!(m.d.F == TF && m.d.lmax == TLMAX) || !a.w->W3sw || !a.err || !a.sched) return MP_ERR_UNSUPPORTED;
     if (a.n == 0) return MP_OK;
-    return a.first ? launch_tc(k_edge_bwd_tc<true>, a, RPG_B, num_sms, st)
-                   : launch_tc(k_edge_bwd_tc<false>, a, RPG_B, num_sms, st);
+    if (a.vir)
+        return a.first ? launch_tc(k_edge_bwd_tc<true, true>, a, RPG_B, num_sms, st)
+                       : launch_tc(k_edge_bwd_tc<false, true>, a, RPG_B, num_sms, st);
+    return a.first ? launch_tc(k_edge_bwd_tc<true, false>, a, RPG_B, num_sms, st)
+                   : launch_tc(k_edge_bwd_tc<false, false>, a, RPG_B, num_sms, st);
 }
 
 }  // namespace mp

@@ -225,6 +225,7 @@ struct BwdSmem {
     float part[CB][NQ][F + 1];
     double red[CB][NQ];
     double frow[RPB][3];
+    double vrow[RPB][9];     // per-row virial sum_e g_e (x) d_e (when requested)
     int row[CB], col[CB];
     int64_t rp[RPB + 1];
 };
@@ -296,6 +297,7 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
     const int nrows = (int)min((int64_t)RPB, a.n - r0);
     if (c <= nrows) s.rp[c] = a.row_ptr[r0 + c];
     if (c < RPB * 3) s.frow[c / 3][c % 3] = 0.0;
+    if (a.vir && c < RPB * 9) s.vrow[c / 9][c % 9] = 0.0;
     __syncthreads();
     const int64_t e_beg = s.rp[0], e_end = s.rp[nrows];
 
@@ -494,6 +496,12 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
                 if (lr < 0) break;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) s.frow[lr][q] += s.red[e][q];
+                if (a.vir) {
+                    const double r = (double)s.u[e][3];
+                    for (int p = 0; p < 3; ++p)
+                        for (int q = 0; q < 3; ++q)
+                            s.vrow[lr][3 * p + q] += s.red[e][p] * ((double)s.u[e][q] * r);
+                }
             }
         }
         __syncthreads();
@@ -505,6 +513,7 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
     for (int q = next; q < nrows; ++q) flush(q, false);
     __syncthreads();
     if (c < nrows * 3) a.frc[(r0 + c / 3) * 3 + c % 3] += s.frow[c / 3][c % 3];
+    if (a.vir && c < nrows * 9) a.vir[(int64_t)(c % 9) * a.vir_stride + r0 + c / 9] += s.vrow[c / 9][c % 9];
 }
 
 template <int F, int LMAX>

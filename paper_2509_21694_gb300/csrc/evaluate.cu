@@ -122,11 +122,13 @@ __global__ void k_pair_term(int64_t n, const int64_t* __restrict__ row_ptr,
                             const int32_t* __restrict__ col, const int8_t* __restrict__ shift,
                             const double* __restrict__ x, EdgeConst k,
                             const uint8_t* __restrict__ seed, double* __restrict__ Ei,
-                            double* __restrict__ frc) {
+                            double* __restrict__ frc, double* __restrict__ vir,
+                            int64_t vir_stride) {
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
     float ei = 0.f, f[3] = {0.f, 0.f, 0.f};
+    double vr[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};    // sum_e (g d) (x) d, when vir
     const float si = seed ? (float)seed[i] : 1.f;
     for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
         const int j = col[e];
@@ -144,12 +146,27 @@ __global__ void k_pair_term(int64_t n, const int64_t* __restrict__ row_ptr,
         f[0] += g * d[0];
         f[1] += g * d[1];
         f[2] += g * d[2];
+        if (vir) {
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) vr[3 * p + q] += (double)(g * d[p]) * (double)d[q];
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ei += __shfl_xor_sync(0xffffffffu, ei, o);
 #pragma unroll
         for (int q = 0; q < 3; ++q) f[q] += __shfl_xor_sync(0xffffffffu, f[q], o);
+    }
+    if (vir) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            double v = vr[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) vir[q * vir_stride + i] += v;
+        }
     }
     if (lane == 0) {
         if (si != 0.f) Ei[i] += (double)ei;   // energies of non-roots are never read
@@ -218,6 +235,16 @@ __global__ void k_sum_final(const double* __restrict__ part, int64_t m, double* 
 
 }  // namespace
 
+__global__ void k_add9(double* __restrict__ acc, const double* __restrict__ v) {
+    if (threadIdx.x < 9) acc[threadIdx.x] += v[threadIdx.x];
+}
+
+// sigma = scale * vtot (scale = 1 / (2 V): every pair is visited from both rows)
+__global__ void k_stress_final(const double* __restrict__ vtot, double scale,
+                               double* __restrict__ stress) {
+    if (threadIdx.x < 9) stress[threadIdx.x] = vtot[threadIdx.x] * scale;
+}
+
 int reduce_sum(const double* v, int64_t n, double* out, DevBuf& tmp, cudaStream_t st) {
     const int64_t per = (int64_t)kRedThreads * kRedItems;
     const int64_t blocks = n > 0 ? (n + per - 1) / per : 1;
@@ -248,6 +275,9 @@ struct EvalBufs {
     float* G[2];
     double* floc;
     double* eloc;
+    double* vloc;     // stress only: per-row virial [9][n_max]; else null
+    double* vsum;     // [9] one sub-system's virial
+    double* vtot;     // [9] all sub-systems', in sub-system order
 };
 
 // Rows a pass must cover: atoms within `hops` hops of a root (a prefix of
@@ -294,6 +324,9 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
     ea.k = kc;
     ea.seed = ss.is_root;
     ea.err = ctx->ws.err.as<int>();
+    ea.vir = b.vloc;
+    ea.vir_stride = n;
+    if (b.vloc) MP_CUDA_TRY(cudaMemsetAsync(b.vloc, 0, sizeof(double) * 9 * n, st));
     ea.sched = ctx->ws.sched.as<int>();
     NodeArgs na{};
     na.inv_navg = kc.inv_navg;
@@ -354,7 +387,7 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         const int64_t n_pair = pre.rows(1);
         if (n_pair > 0) {
             k_pair_term<<<grid_for(n_pair, wpb), 32 * wpb, 0, st>>>(
-                n_pair, ss.row_ptr, ss.col, ss.shift, x, kc, ss.is_root, b.eloc, b.floc);
+                n_pair, ss.row_ptr, ss.col, ss.shift, x, kc, ss.is_root, b.eloc, b.floc, b.vloc, n);
             note_launch();
         }
     }
@@ -407,6 +440,12 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
     k_scatter<<<grid_for(n, 256), 256, 0, st>>>(n, ss.gid, ss.is_root, b.eloc, b.floc, b.e_sorted,
                                                 b.f_sorted);
     note_launch();
+    if (b.vloc) {   // this sub-system's virial, summed in a fixed order
+        for (int q = 0; q < 9; ++q)
+            MP_TRY(reduce_sum(b.vloc + (int64_t)q * n, n, b.vsum + q, ctx->ws.red, st));
+        k_add9<<<1, 32, 0, st>>>(b.vtot, b.vsum);
+        note_launch();
+    }
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
 }
@@ -415,7 +454,7 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
 
 int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,
              const Plan* plan, int K, int precision, int use_head, double* d_energy,
-             float* d_forces, double* d_e_atom) {
+             float* d_forces, double* d_e_atom, double* d_stress) {
     const Model& m = ctx->model;
     if (!d_pos || !d_species || !d_energy || !d_forces) return MP_ERR_ARG;
     if (K < 0 || K > m.d.n_layers_full) return MP_ERR_ARG;
@@ -474,6 +513,14 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
     b.G[1] = ws.G1.as<float>();
     b.floc = ws.floc.as<double>();
     b.eloc = ws.eatom.as<double>();
+    b.vloc = b.vsum = b.vtot = nullptr;
+    if (d_stress) {
+        MP_TRY(ws.vir.reserve(sizeof(double) * (9 * nmax + 18)));
+        b.vloc = ws.vir.as<double>();
+        b.vsum = b.vloc + 9 * nmax;
+        b.vtot = b.vsum + 9;
+        MP_CUDA_TRY(cudaMemsetAsync(b.vtot, 0, sizeof(double) * 9, st));
+    }
 
     k_gather_pos<<<grid_for(n, 256), 256, 0, st>>>(d_pos, d_species, g.perm.as<int32_t>(), n,
                                                    g.box[0], g.box[1], g.box[2], m.d.n_species,
@@ -485,6 +532,10 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
     k_finalize<<<grid_for(n, 256), 256, 0, st>>>(n, g.perm.as<int32_t>(), b.e_sorted, b.f_sorted,
                                                  d_forces, d_e_atom); note_launch();
     MP_TRY(reduce_sum(b.e_sorted, n, d_energy, ws.red, st));
+    if (d_stress) {
+        k_stress_final<<<1, 32, 0, st>>>(b.vtot, 0.5 / (g.box[0] * g.box[1] * g.box[2]), d_stress);
+        note_launch();
+    }
     MP_CUDA_TRY(cudaGetLastError());
     // error word: invalid species; bounded-wait timeouts of the tensor-core kernels
     int herr = 0;

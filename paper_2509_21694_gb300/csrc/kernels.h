@@ -25,6 +25,10 @@ struct EdgeArgs {
     bool first;               // layer 0: input l >= 1 features are zero
     int* err;                 // device error word (bit 2: bounded wait timed out)
     int* sched;               // tensor-core kernels: row-group counter (zeroed per launch)
+    // adjoint, optional: per-row virial sum_e g_e (x) d_e of the pair gradients
+    // g_e added to the row's force, component-major [9][vir_stride], accumulated
+    double* vir;
+    int64_t vir_stride;
 };
 
 int launch_edge_fwd_f32(const Model& m, const EdgeArgs& a, cudaStream_t st);
