@@ -490,18 +490,19 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
             for (int q = 0; q < 3; ++q) s.red[e][q] = gr * u[q] + (v[q] - vu * u[q]) * ir;
         }
         __syncthreads();
-        if (c == 0) {
+        // one thread per output component, each summing the chunk's edges in order
+        if (c < 3) {
             for (int e = 0; e < CB; ++e) {
                 const int lr = s.row[e];
                 if (lr < 0) break;
-#pragma unroll
-                for (int q = 0; q < 3; ++q) s.frow[lr][q] += s.red[e][q];
-                if (a.vir) {
-                    const double r = (double)s.u[e][3];
-                    for (int p = 0; p < 3; ++p)
-                        for (int q = 0; q < 3; ++q)
-                            s.vrow[lr][3 * p + q] += s.red[e][p] * ((double)s.u[e][q] * r);
-                }
+                s.frow[lr][c] += s.red[e][c];
+            }
+        } else if (a.vir && c < 12) {
+            const int p = (c - 3) / 3, q = (c - 3) % 3;
+            for (int e = 0; e < CB; ++e) {
+                const int lr = s.row[e];
+                if (lr < 0) break;
+                s.vrow[lr][3 * p + q] += s.red[e][p] * ((double)s.u[e][q] * (double)s.u[e][3]);
             }
         }
         __syncthreads();
