@@ -29,6 +29,7 @@ STREAM_SPECIES = 0x102
 STREAM_VELOCITY = 0x103
 STREAM_LIQUID = 0x104
 STREAM_SPLIT = 0x105
+STREAM_LANGEVIN = 0x106   # thermostat noise, index (step * N + atom) * 3 + axis
 
 KB_EV = 8.617333262e-5            # Boltzmann constant, eV/K
 KAPPA = 9.648533212e-3            # 1 eV/(Angstrom*amu) in Angstrom/fs^2
@@ -57,9 +58,14 @@ def uniform(seed: int, stream: int, idx) -> np.ndarray:
 
 def normal(seed: int, stream: int, n: int) -> np.ndarray:
     """n standard normals by Box-Muller on draws 2k (radius) and 2k+1 (angle)."""
-    k = np.arange(n, dtype=np.uint64)
-    u1 = 1.0 - uniform(seed, stream, 2 * k)          # (0, 1]: log is finite
-    u2 = uniform(seed, stream, 2 * k + 1)
+    return normal_at(seed, stream, np.arange(n, dtype=np.uint64))
+
+
+def normal_at(seed: int, stream: int, k) -> np.ndarray:
+    """Standard normals number k (any counters) of the construction above."""
+    k = np.asarray(k, dtype=np.uint64)
+    u1 = 1.0 - uniform(seed, stream, np.uint64(2) * k)          # (0, 1]: log is finite
+    u2 = uniform(seed, stream, np.uint64(2) * k + np.uint64(1))
     return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
 
 
