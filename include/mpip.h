@@ -197,11 +197,30 @@ typedef struct {
     int32_t use_head;       /* add the correction head                       */
     int32_t forces_valid;   /* d_forces already holds F(d_pos)               */
     int32_t check_every;    /* read the error word every n steps (0 = end)   */
+    int32_t thermostat;     /* MP_NVE or MP_LANGEVIN                         */
+    int32_t reserved;       /* 0                                             */
+    double temperature;     /* K (Langevin)                                  */
+    double friction;        /* gamma, 1/fs (Langevin)                        */
+    uint64_t seed;          /* noise seed (Langevin)                         */
+    int64_t step0;          /* global index of the first step (Langevin      */
+                            /* noise counters; continue a run with step0 +=  */
+                            /* n_steps)                                      */
 } mp_md_opts;
+#define MP_NVE      0
+#define MP_LANGEVIN 1
 
-/* n_steps velocity-Verlet NVE steps (v += dt/2 a; r += dt v, wrapped; new
- * neighbours, partitions and forces; v += dt/2 a) with a = kappa F / m,
- * kappa = 9.648533212e-3 Angstrom/fs^2 per eV/(Angstrom amu).
+/* n_steps MD steps with a = kappa F / m, kappa = 9.648533212e-3
+ * Angstrom/fs^2 per eV/(Angstrom amu), rebuilding neighbours, partitions and
+ * forces after every position update.
+ * MP_NVE: velocity Verlet (v += dt/2 a; r += dt v, wrapped; F; v += dt/2 a).
+ * MP_LANGEVIN: BAOAB (Leimkuhler and Matthews): v += dt/2 a; r += dt/2 v;
+ *   v = c1 v + c2 sqrt(kB T kappa / m) xi with c1 = exp(-gamma dt),
+ *   c2 = sqrt(1 - c1^2); r += dt/2 v, wrapped; F; v += dt/2 a.  xi is the
+ *   standard normal number k = ((step0 + s) N + i) 3 + a of a counter-based
+ *   generator: u(j) = (splitmix64(seed ^ (0x106 << 40) ^ j) >> 11) 2^-53,
+ *   xi = sqrt(-2 ln(1 - u(2k))) cos(2 pi u(2k + 1)) (atom i in the caller's
+ *   order, step s of this call, axis a).  The paper's MD runs use a Langevin
+ *   thermostat (Results, Table 2 conditions).
  *   d_pos, d_vel  [n][3] double, updated in place (positions stay wrapped).
  *   d_forces      [n][3] float: forces at the final positions on return.
  *   d_mass        [n] double amu.   dt_fs: time step.

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libmpip.so")
 MP_OK = 0
 MP_FP32, MP_BF16 = 0, 1
 MP_HALO_GEOM, MP_HALO_BFS = 0, 1
+MP_NVE, MP_LANGEVIN = 0, 1
 ERRORS = {-1: "MP_ERR_ARG", -2: "MP_ERR_BOX_TOO_SMALL", -3: "MP_ERR_OVERLAP",
           -4: "MP_ERR_CAPACITY", -5: "MP_ERR_CUDA", -6: "MP_ERR_NOT_FINITE",
           -7: "MP_ERR_NOMEM", -8: "MP_ERR_UNSUPPORTED", -9: "MP_ERR_TIMEOUT",
@@ -46,7 +47,10 @@ class mp_md_opts(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("n_parts", ctypes.c_int32), ("k_hops", ctypes.c_int32),
                 ("halo_mode", ctypes.c_int32), ("use_head", ctypes.c_int32),
-                ("forces_valid", ctypes.c_int32), ("check_every", ctypes.c_int32)]
+                ("forces_valid", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("thermostat", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("temperature", ctypes.c_double), ("friction", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("step0", ctypes.c_int64)]
 
 
 def _load():
@@ -257,9 +261,11 @@ def mp_energy_forces_stress(ctx: int, pos: torch.Tensor, species: torch.Tensor, 
 def mp_md_step(ctx: int, pos, vel, forces, mass, species, box, dt: float, n_steps: int,
                n_layers: int, precision: int = MP_FP32, n_parts: int = 1, k_hops: int = 0,
                halo_mode: int = MP_HALO_GEOM, use_head: bool = False, forces_valid: bool = False,
-               check_every: int = 0, ledger: bool = True):
+               check_every: int = 0, ledger: bool = True, thermostat: int = MP_NVE,
+               temperature: float = 0.0, friction: float = 0.0, seed: int = 0, step0: int = 0):
     opts = mp_md_opts(n_layers, precision, n_parts, k_hops, halo_mode, int(use_head),
-                      int(forces_valid), check_every)
+                      int(forces_valid), check_every, thermostat, 0, temperature, friction,
+                      seed, step0)
     b = (ctypes.c_double * 3)(*[float(v) for v in box])
     led = np.zeros((max(n_steps, 1), 3), dtype=np.float64)
     _check(_lib.mp_md_step(ctx, _ptr(pos), _ptr(vel), _ptr(forces), _ptr(mass), _ptr(species),

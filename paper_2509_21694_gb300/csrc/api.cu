@@ -284,11 +284,8 @@ void mp_destroy(mp_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     ctx->model.store.release();
-    Workspace& w = ctx->ws;
-    DevBuf* bufs[] = {&w.xl, &w.sp, &w.H, &w.A, &w.S, &w.G0, &w.G1, &w.alpha, &w.floc,
-                      &w.eatom, &w.esum, &w.fsum, &w.ebuf, &w.err, &w.tmp, &w.xw,
-                      &w.perm_pos, &w.pscr, &w.red, &w.headbuf, &w.adam};
-    for (DevBuf* b : bufs) b->release();
+    ctx->ws.release_all();
+    ctx->md.release_all();
     timing_collect(ctx);
     for (cudaEvent_t e : ctx->timing.pool) cudaEventDestroy(e);
     delete ctx;

@@ -122,6 +122,29 @@ struct Workspace {
     DevBuf xl, sp, H, A, S, G0, G1, alpha, floc, eatom, esum, fsum, ebuf,
         err, tmp, xw, perm_pos, pscr, pstats, red, headbuf, adam, sched, vir,
         corder;   // partition placement: cells in Morton order [ncell], sizes, offsets
+    void release_all() {
+        DevBuf* all[] = {&xl, &sp, &H, &A, &S, &G0, &G1, &alpha, &floc, &eatom, &esum, &fsum,
+                         &ebuf, &err, &tmp, &xw, &perm_pos, &pscr, &pstats, &red, &headbuf,
+                         &adam, &sched, &vir, &corder};
+        for (DevBuf* b : all) b->release();
+    }
+};
+
+// Graph, plan and ledger buffers of mp_md_step, kept by the context so that
+// consecutive calls reuse their device memory.
+struct MdState {
+    Graph g;
+    Plan plan;
+    DevBuf led, scal, ke, red;
+    void release_all() {
+        DevBuf* all[] = {&g.perm, &g.inv, &g.xs, &g.cell_start, &g.row_ptr, &g.col, &g.shift,
+                         &g.scratch, &led, &scal, &ke, &red};
+        for (DevBuf* b : all) b->release();
+        for (Part& P : plan.parts) {
+            P.gid.release(); P.is_root.release(); P.row_ptr.release(); P.col.release();
+            P.shift.release();
+        }
+    }
 };
 
 }  // namespace mp
@@ -150,6 +173,7 @@ struct mp_ctx {
     int device = 0;
     int num_sms = 0;
     mp::Workspace ws;
+    mp::MdState md;
     int* h_err = nullptr;      // pinned host word for error read-back
     int corder_nc[3] = {0, 0, 0};   // cell grid the cached Morton order belongs to
 };

@@ -1,7 +1,14 @@
-// Velocity-Verlet NVE driver (FP64 positions, velocities and energy ledger).
+// MD driver (FP64 positions, velocities and energy ledger).
 //
+// NVE, velocity Verlet:
 //   v += dt/2 kappa F / m;  x += dt v (wrapped);  rebuild neighbours and
 //   partitions;  F = F(x);  v += dt/2 kappa F / m;  KE = sum m v^2 / (2 kappa)
+// Langevin, BAOAB (Leimkuhler and Matthews 2013):
+//   v += dt/2 kappa F / m;  x += dt/2 v;  v = c1 v + c2 sqrt(kB T kappa / m) xi;
+//   x += dt/2 v (wrapped);  F = F(x);  v += dt/2 kappa F / m
+//   with c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2) and xi standard normals
+//   from a counter-based generator: splitmix64 (Steele, Lea and Flood) of
+//   seed ^ (stream << 40) ^ counter, 53-bit uniforms, Box-Muller.
 #include <cmath>
 
 #include "kernels.h"
@@ -26,6 +33,50 @@ __global__ void k_kick_drift(int64_t n, double* __restrict__ x, double* __restri
         double xx = __dadd_rn(x[3 * i + a], __dmul_rn(dt, vv));
         xx = __dsub_rn(xx, __dmul_rn(L[a], floor(__ddiv_rn(xx, L[a]))));
         if (xx >= L[a]) xx = __dsub_rn(xx, L[a]);
+        x[3 * i + a] = xx;
+    }
+}
+
+// Counter-based standard normal number k of the Langevin stream.
+constexpr uint64_t kStreamLangevin = 0x106;
+
+__device__ __forceinline__ uint64_t splitmix64_dev(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double uniform_dev(uint64_t seed, uint64_t j) {
+    const uint64_t key = seed ^ (kStreamLangevin << 40) ^ j;
+    return (double)(splitmix64_dev(key) >> 11) * 0x1.0p-53;
+}
+
+__device__ __forceinline__ double normal_dev(uint64_t seed, uint64_t k) {
+    const double u1 = 1.0 - uniform_dev(seed, 2 * k);     // (0, 1]
+    const double u2 = uniform_dev(seed, 2 * k + 1);
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
+}
+
+// B, A, O and A of a BAOAB step (the closing B follows the force update).
+__global__ void k_baoab(int64_t n, double* __restrict__ x, double* __restrict__ v,
+                        const float* __restrict__ f, const double* __restrict__ m, double dt,
+                        double L0, double L1, double L2, double c1, double c2, double kt_kappa,
+                        uint64_t seed, uint64_t k0) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double c = 0.5 * dt * kKappa / m[i];
+    const double sig = sqrt(kt_kappa / m[i]);
+    const double L[3] = {L0, L1, L2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double vv = v[3 * i + a] + c * (double)f[3 * i + a];
+        double xx = x[3 * i + a] + 0.5 * dt * vv;
+        vv = c1 * vv + c2 * sig * normal_dev(seed, k0 + 3 * (uint64_t)i + a);
+        xx = xx + 0.5 * dt * vv;
+        xx = __dsub_rn(xx, __dmul_rn(L[a], floor(__ddiv_rn(xx, L[a]))));
+        if (xx >= L[a]) xx = __dsub_rn(xx, L[a]);
+        v[3 * i + a] = vv;
         x[3 * i + a] = xx;
     }
 }
@@ -59,16 +110,22 @@ int md_run(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const dou
            const mp_md_opts* o, double* h_ledger) {
     if (!o || n <= 0 || n_steps < 0 || !d_pos || !d_vel || !d_forces || !d_mass || !d_species)
         return MP_ERR_ARG;
+    if (o->thermostat != MP_NVE && o->thermostat != MP_LANGEVIN) return MP_ERR_ARG;
+    if (o->thermostat == MP_LANGEVIN && !(o->temperature >= 0.0 && o->friction >= 0.0))
+        return MP_ERR_ARG;
     cudaStream_t st = ctx->stream;
-    DevBuf led, scal, ke, red;
+    MdState& md = ctx->md;
+    DevBuf &led = md.led, &scal = md.scal, &ke = md.ke, &red = md.red;
     MP_TRY(led.reserve(sizeof(double) * 3 * (n_steps > 0 ? n_steps : 1)));
     MP_TRY(scal.reserve(sizeof(double) * 4));
     MP_TRY(ke.reserve(sizeof(double) * n));
     double* pe = scal.as<double>();
     double* kes = pe + 1;
-    Graph g;
-    Plan plan;
+    Graph& g = md.g;
+    Plan& plan = md.plan;
     int rc = MP_OK;
+    const double c1 = exp(-o->friction * dt), c2 = sqrt(1.0 - c1 * c1);
+    const double kt_kappa = 8.617333262e-5 * o->temperature * kKappa;   // kB T kappa
     auto forces = [&]() -> int {
         MP_TRY(build_graph(ctx, d_pos, n, box, g));
         const Plan* pp = nullptr;
@@ -83,8 +140,14 @@ int md_run(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const dou
     };
     if (!o->forces_valid) rc = forces();
     for (int s = 0; s < n_steps && rc == MP_OK; ++s) {
-        k_kick_drift<<<grid_for(n, 256), 256, 0, st>>>(n, d_pos, d_vel, d_forces, d_mass, dt,
-                                                       box[0], box[1], box[2]); note_launch();
+        if (o->thermostat == MP_LANGEVIN)
+            k_baoab<<<grid_for(n, 256), 256, 0, st>>>(
+                n, d_pos, d_vel, d_forces, d_mass, dt, box[0], box[1], box[2], c1, c2, kt_kappa,
+                o->seed, (uint64_t)(o->step0 + s) * 3 * (uint64_t)n);
+        else
+            k_kick_drift<<<grid_for(n, 256), 256, 0, st>>>(n, d_pos, d_vel, d_forces, d_mass, dt,
+                                                           box[0], box[1], box[2]);
+        note_launch();
         rc = forces();
         if (rc) break;
         k_kick_ke<<<grid_for(n, 256), 256, 0, st>>>(n, d_vel, d_forces, d_mass, dt,
@@ -115,17 +178,7 @@ int md_run(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const dou
         }
     }
     cudaStreamSynchronize(st);
-    led.release();
-    scal.release();
-    ke.release();
-    red.release();
-    g.perm.release(); g.inv.release(); g.xs.release(); g.cell_start.release();
-    g.row_ptr.release(); g.col.release(); g.shift.release(); g.scratch.release();
-    for (Part& P : plan.parts) {
-        P.gid.release(); P.is_root.release(); P.row_ptr.release(); P.col.release();
-        P.shift.release();
-    }
-    return rc;
+    return rc;   // graph, plan and ledger buffers stay with the context for the next call
 }
 
 }  // namespace mp
