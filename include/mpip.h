@@ -186,6 +186,21 @@ int mp_energy_forces_stress(mp_ctx* ctx, const double* d_pos, const int32_t* d_s
                             int use_head, double* d_energy, float* d_forces, double* d_e_atom,
                             double* d_stress);
 
+/* ---- layer diagnostics ---------------------------------------------------
+ * Methods, "Mean Feature Shift and Linear CKA": for the scalar features h0
+ * (N x F) after each layer t = 0..n_layers of one unpartitioned evaluation
+ * (t = 0: the embedding), centred H~ = H - (1/N) 1 1^T H:
+ *   h_mfs[t] = (1/N) || H~(t+1) - H~(t) ||_F
+ *   h_cka[t] = || H~(t)^T H~(t+1) ||_F^2
+ *              / (|| H~(t)^T H~(t) ||_F || H~(t+1)^T H~(t+1) ||_F)
+ * for t = 0..n_layers-1 (host arrays of n_layers doubles).  Sums in FP64, in
+ * a fixed order.  Synchronises the stream.
+ * Errors: MP_ERR_ARG (n_layers < 1 or above L_full), MP_ERR_UNSUPPORTED
+ * (F not a multiple of 32), those of mp_energy_forces. */
+int mp_layer_stats(mp_ctx* ctx, const double* d_pos, const int32_t* d_species,
+                   const mp_graph* g, int n_layers, int precision, double* h_mfs,
+                   double* h_cka);
+
 /* ---- molecular dynamics ------------------------------------------------ */
 typedef struct {
     int32_t n_layers;       /* K                                             */

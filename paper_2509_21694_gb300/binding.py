@@ -76,6 +76,7 @@ def _load():
         "mp_plan_free": (None, [P]),
         "mp_energy_forces": (I32, [P, P, P, P, P, I32, I32, I32, P, P, P]),
         "mp_energy_forces_stress": (I32, [P, P, P, P, P, I32, I32, I32, P, P, P, P]),
+        "mp_layer_stats": (I32, [P, P, P, P, I32, I32, P, P]),
         "mp_md_step": (I32, [P, P, P, P, P, P, I64, ctypes.POINTER(D), D, I32,
                              ctypes.POINTER(mp_md_opts), P]),
         "mp_kernel_launches": (I32, [ctypes.POINTER(I64)]),
@@ -256,6 +257,16 @@ def mp_energy_forces_stress(ctx: int, pos: torch.Tensor, species: torch.Tensor, 
                                         precision, int(use_head), _ptr(energy), _ptr(forces),
                                         _ptr(e_atom), _ptr(stress)), "mp_energy_forces_stress")
     return energy, forces, e_atom, stress
+
+
+def mp_layer_stats(ctx: int, pos: torch.Tensor, species: torch.Tensor, g: int, n_layers: int,
+                   precision: int = MP_FP32):
+    """(MFS, CKA) numpy arrays of length n_layers for the transitions t -> t + 1."""
+    mfs = np.zeros(n_layers, dtype=np.float64)
+    cka = np.zeros(n_layers, dtype=np.float64)
+    _check(_lib.mp_layer_stats(ctx, _ptr(pos), _ptr(species), g, n_layers, precision,
+                               mfs.ctypes.data, cka.ctypes.data), "mp_layer_stats")
+    return mfs, cka
 
 
 def mp_md_step(ctx: int, pos, vel, forces, mass, species, box, dt: float, n_steps: int,

@@ -200,6 +200,9 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
 int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,
              const Plan* plan, int n_layers, int precision, int use_head, double* d_energy,
              float* d_forces, double* d_e_atom, double* d_stress = nullptr);
+// diagnostics.cu
+int layer_stats(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g, int K,
+                int precision, double* h_mfs, double* h_cka);
 // head.cu
 int64_t head_param_count(const Model& m);
 int head_loss_grad(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,
