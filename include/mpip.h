@@ -194,7 +194,8 @@ int mp_energy_forces_stress(mp_ctx* ctx, const double* d_pos, const int32_t* d_s
  *   h_cka[t] = || H~(t)^T H~(t+1) ||_F^2
  *              / (|| H~(t)^T H~(t) ||_F || H~(t+1)^T H~(t+1) ||_F)
  * for t = 0..n_layers-1 (host arrays of n_layers doubles).  Sums in FP64, in
- * a fixed order.  Synchronises the stream.
+ * a fixed order.  The CKA is NaN when a layer's centred features vanish
+ * (e.g. the embedding of a one-species system).  Synchronises the stream.
  * Errors: MP_ERR_ARG (n_layers < 1 or above L_full), MP_ERR_UNSUPPORTED
  * (F not a multiple of 32), those of mp_energy_forces. */
 int mp_layer_stats(mp_ctx* ctx, const double* d_pos, const int32_t* d_species,
