@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--atoms", type=int, default=32000, help="atoms of the liquid")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--study", default=None, choices=["partition"],
+                    help="partition: Stage 1 by spatial grid vs the graph partitioner "
+                         "(time, halo factor, cut, balance, MD throughput), one JSON line "
+                         "per system, instead of the benchmark line")
     return ap.parse_args()
 
 
@@ -337,6 +341,120 @@ def run_ours(args, rank, world):
     return out
 
 
+# ------------------------------------------- partitioning study (GPU) --
+
+STUDY_SYSTEMS = {
+    # bulk FCC Cu (cells per axis) and Ni-supported Cu particles
+    # (cells_xy, support cells, particle radius, particle grid)
+    "bulk-32k": ("fcc", 20),
+    "bulk-131k": ("fcc", 32),
+    "bulk-1M": ("fcc", 64),
+    "particles-12k": ("particles", ((24, 24), 4, 12.0, (2, 2))),
+    "particles-92k": ("particles", ((48, 48), 8, 18.0, (3, 3))),
+    "particles-364k": ("particles", ((64, 64), 16, 26.0, (4, 4))),
+}
+
+
+def run_partition_study(args):
+    """Stage 1 compared on bulk and heterogeneous systems (Supplementary S1,
+    Figs. S1-S2): the z grid (the benchmark's slabs), a grid along x (in the
+    support plane) and the multilevel graph partitioner, each with a K-hop
+    BFS halo.  Reports wall time of each partitioning call, the halo growth
+    factor H, the edge cut, the largest part over the mean, and the BF16 MD
+    throughput with z slabs and with the graph parts."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2509_21694_gb300 import build
+    build.build()
+    from paper_2509_21694_gb300 import binding as mp
+
+    dev = torch.device("cuda", 0)
+    P, K = args.parts, args.layers
+    lines = []
+    for name, (kind, spec) in STUDY_SYSTEMS.items():
+        if kind == "fcc":
+            s = synth.cu_fcc_large(cells=(spec,) * 3, sigma=0.05, seed=4)
+            d = synth.model_cu(n_layers_full=6)
+            w = synth.make_weights(d, 4)
+        else:
+            cxy, sc, rad, grid = spec
+            s = synth.supported_particles(cells_xy=cxy, slab_cells=sc, radius=rad, grid=grid,
+                                          seed=5)
+            d = synth.model_alloy(n_layers_full=6)
+            w = synth.make_weights(d, 1)
+        n = len(s.pos)
+        ctx = mp.mp_create(d, w)
+        stream = torch.cuda.current_stream()
+        mp.mp_set_stream(ctx, stream.cuda_stream)
+        pos = torch.tensor(s.pos, device=dev)
+        g = mp.mp_build_neighbors(ctx, pos, s.box)
+        recv, send, _ = mp.mp_graph_export(g)
+        recv, send = recv.long(), send.long()
+
+        def describe(part, H, ms):
+            a = part.long()
+            cut = int((a[recv] != a[send]).sum().item()) // 2
+            wts = torch.bincount(a, minlength=P).cpu().numpy()
+            return {"H": H, "cut": cut, "max_over_mean": float(wts.max() / (n / P)),
+                    "ms": ms}
+
+        def timed(fn):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            return r, (time.perf_counter() - t) * 1e3
+
+        # warm the library's buffers once, then time
+        plan, _ = mp.mp_partition(ctx, g, P, K, mp.MP_HALO_BFS)
+        mp.mp_plan_free(plan)
+        (plan, Hz), ms_z = timed(lambda: mp.mp_partition(ctx, g, P, K, mp.MP_HALO_BFS))
+        mp.mp_plan_free(plan)
+        x = torch.remainder(pos, torch.tensor(s.box, device=dev))
+        zb = torch.clamp((x[:, 2] / s.box[2] * P).floor().int(), max=P - 1).contiguous()
+        xb = torch.clamp((x[:, 0] / s.box[0] * P).floor().int(), max=P - 1).contiguous()
+        plan, Hx = mp.mp_partition_assign(ctx, g, xb, P, K)
+        mp.mp_plan_free(plan)
+        mp.mp_graph_partition(ctx, g, P, 0.03, seed=1)
+        (gres, ms_g) = timed(lambda: mp.mp_graph_partition(ctx, g, P, 0.03, seed=1))
+        part, _ = gres
+        plan, Hg = mp.mp_partition_assign(ctx, g, part, P, K)
+        mp.mp_plan_free(plan)
+        row = {"study": "partition", "system": name, "n_atoms": n, "n_edges": int(recv.numel()),
+               "n_parts": P, "k_hops": K,
+               "grid_z": describe(zb, Hz, ms_z), "grid_x": describe(xb, Hx, None),
+               "graph": describe(part, Hg, ms_g)}
+        mp.mp_graph_free(g)
+
+        # MD throughput, BF16, K layers, P partitions: z slabs vs graph parts
+        v0 = torch.tensor(synth.maxwell(s.masses, 600.0, 4), device=dev)
+        mass = torch.tensor(s.masses, device=dev)
+        sp = torch.tensor(s.species, device=dev)
+        md_rate = {}
+        for label, extra in (("grid_z", dict(halo_mode=mp.MP_HALO_BFS)),
+                             ("graph", dict(part=part))):
+            p_ = pos.clone()
+            v_ = v0.clone()
+            f_ = torch.zeros(n, 3, dtype=torch.float32, device=dev)
+            common = dict(n_layers=K, precision=mp.MP_BF16, n_parts=P, k_hops=K)
+            mp.mp_md_step(ctx, p_, v_, f_, mass, sp, s.box, 1.0, 2, **common, **extra)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mp.mp_md_step(ctx, p_, v_, f_, mass, sp, s.box, 1.0, args.steps, forces_valid=True,
+                          **common, **extra)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            md_rate[label] = n * args.steps / (e0.elapsed_time(e1) * 1e-3)
+        row["md_atom_steps_per_s"] = md_rate
+        mp.mp_destroy(ctx)
+        print(json.dumps(row), flush=True)
+        lines.append(row)
+    return lines
+
+
 # ------------------------------------------------------ oracle (CPU) --
 
 def oracle_sample_step(args, cells=6):
@@ -403,6 +521,9 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.study == "partition":
+        run_partition_study(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

@@ -140,6 +140,40 @@ void mp_graph_free(mp_graph* g);
  * Errors: MP_ERR_ARG, MP_ERR_NOMEM, MP_ERR_CUDA. */
 int mp_partition(mp_ctx* ctx, const mp_graph* g, int n_parts, int k_hops, int mode,
                  mp_plan** plan_out, double* halo_factor_out);
+/* Partitions whose roots a caller gives (Stage 1 by any partitioner, e.g.
+ * mp_graph_partition for heterogeneous geometries), halos by k_hops BFS
+ * expansions over the graph (Stage 2).  The partitioned result is exact for
+ * any assignment: every root keeps its k_hops-hop neighbourhood.
+ *   d_part  [n] int32 device, caller's atom order: partition of each atom,
+ *           in 0..n_parts-1 (checked on the device; an entry outside the
+ *           range makes the call return MP_ERR_ARG).  Not kept by the plan.
+ *   halo_factor_out  as for mp_partition.
+ * Plans export and evaluate like those of mp_partition (hop classes are BFS
+ * levels).  Synchronises once.  Errors: MP_ERR_ARG, MP_ERR_NOMEM,
+ * MP_ERR_CUDA. */
+int mp_partition_assign(mp_ctx* ctx, const mp_graph* g, const int32_t* d_part, int n_parts,
+                        int k_hops, mp_plan** plan_out, double* halo_factor_out);
+
+/* Multilevel k-way graph partitioner (Methods, "Graph Partitioning": a
+ * METIS-like partitioner for nanoparticles on supports and other
+ * heterogeneous geometries, where uniform bins give unbalanced or
+ * fragmented subgraphs; Supplementary S1 compares its halo growth factor
+ * with the spatial grid's).  Minimises the number of cut edges subject to
+ * every part's atom count <= max(ceil(N / n_parts),
+ * floor((1 + imbalance) N / n_parts)).  Coarsening (heavy-edge matching and
+ * contraction) and k-way boundary refinement run on the GPU; the coarsest
+ * graph (at most max(1024, 128 n_parts) vertices unless matching stalls) is
+ * split on the host by recursive greedy bisection.  The result is a
+ * function of the graph and the seed only.
+ *   n_parts       1..64, <= N.   imbalance  >= 0 (e.g. 0.03).
+ *   d_part        [n] int32 device, written, caller's atom order.
+ *   edge_cut_out  host, may be NULL: number of cut (undirected) edges.
+ * Allocates and frees its own scratch; synchronises the stream several
+ * times.  Errors: MP_ERR_ARG, MP_ERR_NOMEM, MP_ERR_CUDA, MP_ERR_UNSUPPORTED
+ * (a coarse vertex with more than 16384 edge entries to merge). */
+int mp_graph_partition(mp_ctx* ctx, const mp_graph* g, int n_parts, double imbalance,
+                       uint64_t seed, int32_t* d_part, int64_t* edge_cut_out);
+
 /* Host read-back: sizes of partition p. */
 int mp_plan_info(const mp_plan* plan, int p, int64_t* n_ext, int64_t* n_root, int64_t* n_edges);
 /* Extended set of partition p in caller ids and a root flag per entry:
@@ -221,6 +255,9 @@ typedef struct {
     int64_t step0;          /* global index of the first step (Langevin      */
                             /* noise counters; continue a run with step0 +=  */
                             /* n_steps)                                      */
+    const int32_t* d_part;  /* NULL = z slabs; else [n] int32 device roots   */
+                            /* per atom (caller order, as for                */
+                            /* mp_partition_assign), halos by BFS            */
 } mp_md_opts;
 #define MP_NVE      0
 #define MP_LANGEVIN 1

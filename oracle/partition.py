@@ -26,6 +26,11 @@ every partition that holds them).
 
 Halo growth factor (Supplementary S1): H = (#halo atoms) / (#root atoms).
 
+Stage 1 may also come from a graph partitioner (the paper uses METIS for
+heterogeneous geometries): ``assignment_plan`` takes any per-atom
+assignment and extends it by BFS; ``edge_cut`` and ``part_weights`` give the
+two quantities such a partitioner trades off.
+
 Parity pins: the partitioned E and F equal the unpartitioned ones (the
 paper's exactness claim), BFS and geometric halos give equal root outputs,
 the BFS set is contained in the geometric set, and roots cover every atom
@@ -89,6 +94,38 @@ def plan(pos, box, edges, n_parts: int, k_hops: int, r_cut: float, mode: str = "
         parts.append((roots, ext))
     H = n_halo / pos.shape[0]
     return parts, H
+
+
+def assignment_plan(assign, edges, n_parts: int, k_hops: int):
+    """Stage 1 by any partitioner, then Stage 2 by BFS: partition p has the
+    roots {i : assign[i] = p} and their k_hops-hop neighbourhood (Methods,
+    "Graph Partitioning"; the graph-based Stage 1 for heterogeneous systems).
+    Returns the list of (roots_mask, extended_mask) and the halo factor H."""
+    recv, send, _ = edges
+    assign = np.asarray(assign)
+    parts = []
+    n_halo = 0
+    for p in range(n_parts):
+        roots = assign == p
+        ext = bfs_halo(roots, recv, send, k_hops)
+        n_halo += int(ext.sum() - roots.sum())
+        parts.append((roots, ext))
+    return parts, n_halo / assign.shape[0]
+
+
+def edge_cut(assign, edges) -> int:
+    """Undirected edges whose ends lie in different parts (each pair appears
+    twice in the directed edge set)."""
+    recv, send, _ = edges
+    assign = np.asarray(assign)
+    crossing = int((assign[recv] != assign[send]).sum())
+    assert crossing % 2 == 0
+    return crossing // 2
+
+
+def part_weights(assign, n_parts: int) -> np.ndarray:
+    """Atoms per part."""
+    return np.bincount(np.asarray(assign), minlength=n_parts)
 
 
 def sub_edges(edges, ext_mask):

@@ -50,7 +50,8 @@ class mp_md_opts(ctypes.Structure):
                 ("forces_valid", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("thermostat", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("temperature", ctypes.c_double), ("friction", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("step0", ctypes.c_int64)]
+                ("seed", ctypes.c_uint64), ("step0", ctypes.c_int64),
+                ("d_part", ctypes.c_void_p)]
 
 
 def _load():
@@ -70,6 +71,8 @@ def _load():
         "mp_graph_export": (I32, [P, P, P, P]),
         "mp_graph_free": (None, [P]),
         "mp_partition": (I32, [P, P, I32, I32, I32, PP, ctypes.POINTER(D)]),
+        "mp_partition_assign": (I32, [P, P, P, I32, I32, PP, ctypes.POINTER(D)]),
+        "mp_graph_partition": (I32, [P, P, I32, D, ctypes.c_uint64, P, ctypes.POINTER(I64)]),
         "mp_plan_info": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64),
                                ctypes.POINTER(I64)]),
         "mp_plan_export": (I32, [P, I32, P, P]),
@@ -211,6 +214,28 @@ def mp_partition(ctx: int, g: int, n_parts: int, k_hops: int, mode: int = MP_HAL
     return p.value, H.value
 
 
+def mp_partition_assign(ctx: int, g: int, part: torch.Tensor, n_parts: int, k_hops: int):
+    """Plan with the roots of ``part`` (int32 [n] device, caller order) and BFS halos."""
+    assert part.dtype == torch.int32 and part.is_cuda and part.is_contiguous()
+    p = ctypes.c_void_p()
+    H = ctypes.c_double()
+    _check(_lib.mp_partition_assign(ctx, g, _ptr(part), n_parts, k_hops, ctypes.byref(p),
+                                    ctypes.byref(H)), "mp_partition_assign")
+    return p.value, H.value
+
+
+def mp_graph_partition(ctx: int, g: int, n_parts: int, imbalance: float = 0.03, seed: int = 0,
+                       part: torch.Tensor | None = None):
+    """(part int32 [n] device in caller order, number of cut edges)."""
+    n, _ = mp_graph_info(g)
+    if part is None:
+        part = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    cut = ctypes.c_int64()
+    _check(_lib.mp_graph_partition(ctx, g, n_parts, imbalance, seed, _ptr(part),
+                                   ctypes.byref(cut)), "mp_graph_partition")
+    return part[:n], cut.value
+
+
 def mp_plan_info(plan: int, p: int):
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(_lib.mp_plan_info(plan, p, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
@@ -273,10 +298,14 @@ def mp_md_step(ctx: int, pos, vel, forces, mass, species, box, dt: float, n_step
                n_layers: int, precision: int = MP_FP32, n_parts: int = 1, k_hops: int = 0,
                halo_mode: int = MP_HALO_GEOM, use_head: bool = False, forces_valid: bool = False,
                check_every: int = 0, ledger: bool = True, thermostat: int = MP_NVE,
-               temperature: float = 0.0, friction: float = 0.0, seed: int = 0, step0: int = 0):
+               temperature: float = 0.0, friction: float = 0.0, seed: int = 0, step0: int = 0,
+               part: torch.Tensor | None = None):
+    """``part``: per-atom roots (int32 [n] device, caller order) instead of z slabs."""
+    if part is not None:
+        assert part.dtype == torch.int32 and part.is_cuda and part.is_contiguous()
     opts = mp_md_opts(n_layers, precision, n_parts, k_hops, halo_mode, int(use_head),
                       int(forces_valid), check_every, thermostat, 0, temperature, friction,
-                      seed, step0)
+                      seed, step0, _ptr(part) if part is not None else None)
     b = (ctypes.c_double * 3)(*[float(v) for v in box])
     led = np.zeros((max(n_steps, 1), 3), dtype=np.float64)
     _check(_lib.mp_md_step(ctx, _ptr(pos), _ptr(vel), _ptr(forces), _ptr(mass), _ptr(species),
@@ -374,15 +403,20 @@ class Potential:
             pass
 
     def energy_forces(self, pos, species, box, n_layers, precision=MP_FP32, n_parts=1,
-                      k_hops=None, halo_mode=MP_HALO_GEOM, use_head=False, per_atom=False):
-        """Neighbours, optional partition plan and E/F in one call."""
+                      k_hops=None, halo_mode=MP_HALO_GEOM, use_head=False, per_atom=False,
+                      part=None):
+        """Neighbours, optional partition plan and E/F in one call.  ``part``
+        (int32 [n] device, caller order) gives the roots of each of the
+        n_parts partitions instead of z slabs; halos are then BFS."""
         mp_set_stream(self.ctx, _stream())
         g = mp_build_neighbors(self.ctx, pos, box)
         plan = None
         try:
-            if n_parts > 1:
-                plan, _ = mp_partition(self.ctx, g, n_parts,
-                                       n_layers if k_hops is None else k_hops, halo_mode)
+            hops = n_layers if k_hops is None else k_hops
+            if part is not None:
+                plan, _ = mp_partition_assign(self.ctx, g, part, n_parts, hops)
+            elif n_parts > 1:
+                plan, _ = mp_partition(self.ctx, g, n_parts, hops, halo_mode)
             e_atom = (torch.empty(pos.shape[0], dtype=torch.float64, device=pos.device)
                       if per_atom else None)
             E, F, e_atom = mp_energy_forces(self.ctx, pos, species, g, plan, n_layers, precision,

@@ -346,6 +346,29 @@ int mp_partition(mp_ctx* ctx, const mp_graph* g, int n_parts, int k_hops, int mo
     return MP_OK;
 }
 
+int mp_partition_assign(mp_ctx* ctx, const mp_graph* g, const int32_t* d_part, int n_parts,
+                        int k_hops, mp_plan** plan_out, double* halo_factor_out) {
+    if (!ctx || !g || !d_part || !plan_out) return MP_ERR_ARG;
+    *plan_out = nullptr;
+    mp_plan* p = new (std::nothrow) mp_plan();
+    if (!p) return MP_ERR_NOMEM;
+    p->ctx = ctx;
+    p->graph = g;
+    int rc = build_plan(ctx, g->g, n_parts, k_hops, MP_HALO_BFS, p->p, halo_factor_out, d_part);
+    if (rc != MP_OK) {
+        mp_plan_free(p);
+        return rc;
+    }
+    *plan_out = p;
+    return MP_OK;
+}
+
+int mp_graph_partition(mp_ctx* ctx, const mp_graph* g, int n_parts, double imbalance,
+                       uint64_t seed, int32_t* d_part, int64_t* edge_cut_out) {
+    if (!ctx || !g || !d_part) return MP_ERR_ARG;
+    return graph_partition(ctx, g->g, n_parts, imbalance, seed, d_part, edge_cut_out);
+}
+
 int mp_plan_info(const mp_plan* plan, int p, int64_t* n_ext, int64_t* n_root, int64_t* n_edges) {
     if (!plan || p < 0 || p >= plan->p.n_parts) return MP_ERR_ARG;
     const Part& P = plan->p.parts[p];

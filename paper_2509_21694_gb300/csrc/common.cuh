@@ -37,6 +37,18 @@ struct DevBuf {
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// Releases function-local buffers when the scope ends, early error returns
+// included (DevBuf itself does not own its memory past release()).
+struct BufGuard {
+    std::vector<DevBuf*> bufs;
+    BufGuard(std::initializer_list<DevBuf*> b) : bufs(b) {}
+    BufGuard(const BufGuard&) = delete;
+    BufGuard& operator=(const BufGuard&) = delete;
+    ~BufGuard() {
+        for (DevBuf* b : bufs) b->release();
+    }
+};
+
 // Device copies of one layer's weights.  *T arrays are transposed
 // ([in][out]) so that a thread owning an output channel reads coalesced.
 struct LayerW {
@@ -195,7 +207,10 @@ namespace mp {
 int build_graph(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3], Graph& g);
 // partition.cu
 int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, Plan& plan,
-               double* halo_factor);
+               double* halo_factor, const int32_t* d_assign = nullptr);
+// gpart.cu
+int graph_partition(mp_ctx* ctx, const Graph& g, int k, double imbalance, uint64_t seed,
+                    int32_t* d_out, int64_t* cut_out);
 // evaluate.cu
 int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,
              const Plan* plan, int n_layers, int precision, int use_head, double* d_energy,

@@ -122,6 +122,7 @@ int layer_stats(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, cons
     const int64_t n = g.n;
     cudaStream_t st = ctx->stream;
     DevBuf ef, stats;
+    BufGuard guard{&ef, &stats};
     MP_TRY(ef.reserve(sizeof(double) + sizeof(float) * 3 * n + 64));
     MP_TRY(evaluate(ctx, d_pos, d_species, g, nullptr, K, precision, 0, ef.as<double>(),
                     reinterpret_cast<float*>(ef.as<double>() + 1), nullptr));

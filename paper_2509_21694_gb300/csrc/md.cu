@@ -132,7 +132,8 @@ int md_run(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const dou
         if (o->n_parts > 1) {
             // the halo must reach K hops for the partitioned result to be exact
             const int hops = o->k_hops > 0 ? o->k_hops : o->n_layers;
-            MP_TRY(build_plan(ctx, g, o->n_parts, hops, o->halo_mode, plan, nullptr));
+            MP_TRY(build_plan(ctx, g, o->n_parts, hops, o->d_part ? MP_HALO_BFS : o->halo_mode,
+                              plan, nullptr, o->d_part));
             pp = &plan;
         }
         return evaluate(ctx, d_pos, d_species, g, pp, o->n_layers, o->precision, o->use_head, pe,

@@ -1,7 +1,8 @@
 // Spatial-grid partitions with ghost halos and local CSR extraction.
 //
 // Stage 1 (Methods, "Graph Partitioning"): P uniform bins of the scaled z
-// coordinate, root bin = min(floor(x_w,z / L_z * P), P - 1).
+// coordinate, root bin = min(floor(x_w,z / L_z * P), P - 1), or the roots a
+// caller-given assignment names (a graph partitioner's output).
 // Stage 2: every root keeps its K-hop neighbourhood, either by K BFS
 // expansions over the global CSR (MP_HALO_BFS) or by the geometric slab
 // halo of width K r_c (MP_HALO_GEOM, a superset: each hop is shorter than
@@ -105,6 +106,24 @@ __global__ void k_class_root(const double* __restrict__ xs, int64_t n, double Lz
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     cls[s] = root_bin(xs[3 * s + 2], Lz, P) == p ? 0 : K + 1;
+}
+
+// Roots from a caller-given assignment (Stage 1 by any partitioner):
+// assign[perm[s]] is the partition of sorted atom s.
+__global__ void k_class_assign(const int32_t* __restrict__ assign, const int32_t* __restrict__ perm,
+                               int64_t n, int p, int K, int32_t* __restrict__ cls) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    cls[s] = assign[perm[s]] == p ? 0 : K + 1;
+}
+
+// Number of assignment entries outside [0, P).
+__global__ void k_check_assign(const int32_t* __restrict__ assign, int64_t n, int P,
+                               unsigned long long* __restrict__ bad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t a = assign[i];
+    if (a < 0 || a >= P) atomicAdd(bad, 1ull);
 }
 
 // BFS level h: an atom outside the set joins at level h if a neighbour has a
@@ -216,9 +235,11 @@ std::vector<int32_t> morton_cell_order(const int nc[3]) {
 }  // namespace
 
 int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, Plan& plan,
-               double* halo_factor) {
+               double* halo_factor, const int32_t* d_assign) {
     if (n_parts < 1 || k_hops < 0 || (mode != MP_HALO_GEOM && mode != MP_HALO_BFS))
         return MP_ERR_ARG;
+    // an arbitrary root set has no slab to measure a geometric halo from
+    if (d_assign && mode != MP_HALO_BFS) return MP_ERR_ARG;
     cudaStream_t st = ctx->stream;
     const int64_t n = g.n;
     const int K = k_hops;
@@ -272,9 +293,19 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
     // back in one copy at the end.
     DevBuf& stats = ws.pstats;
     const int ns = 2 * (K + 1);
-    MP_TRY(stats.reserve(sizeof(int64_t) * n_parts * ns + sizeof(int32_t) * n_parts * (K + 1)));
+    // per partition: ns sizes; then one slot for the count of invalid
+    // assignment entries; then the class counts
+    MP_TRY(stats.reserve(sizeof(int64_t) * (n_parts * ns + 1) +
+                         sizeof(int32_t) * n_parts * (K + 1)));
     int64_t* d_stats = stats.as<int64_t>();
-    int32_t* d_cnt = reinterpret_cast<int32_t*>(d_stats + (size_t)n_parts * ns);
+    int64_t* d_bad = d_stats + (size_t)n_parts * ns;
+    int32_t* d_cnt = reinterpret_cast<int32_t*>(d_bad + 1);
+    MP_CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int64_t), st));
+    if (d_assign) {
+        k_check_assign<<<grid_for(n, 256), 256, 0, st>>>(
+            d_assign, n, n_parts, reinterpret_cast<unsigned long long*>(d_bad));
+        note_launch();
+    }
     for (int p = 0; p < n_parts; ++p) {
         Part& P = plan.parts[p];
         int32_t* cnt = d_cnt + (size_t)p * (K + 1);
@@ -283,7 +314,11 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
             k_class_geom<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, rc, K, cls);
             note_launch();
         } else {
-            k_class_root<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, K, cls);
+            if (d_assign)
+                k_class_assign<<<grid_for(n, 256), 256, 0, st>>>(d_assign, g.perm.as<int32_t>(),
+                                                                 n, p, K, cls);
+            else
+                k_class_root<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, K, cls);
             note_launch();
             int32_t* other = cls2;
             for (int h = 1; h <= K; ++h) {
@@ -323,10 +358,11 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
         k_plan_stats<<<1, 32, 0, st>>>(cnt, K, P.row_ptr.as<int64_t>(), d_stats + (size_t)p * ns);
         note_launch();
     }
-    std::vector<int64_t> h_stats((size_t)n_parts * ns);
+    std::vector<int64_t> h_stats((size_t)n_parts * ns + 1);
     MP_CUDA_TRY(cudaMemcpyAsync(h_stats.data(), d_stats, sizeof(int64_t) * h_stats.size(),
                                 cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_stats[(size_t)n_parts * ns] != 0) return MP_ERR_ARG;   // assignment outside [0, P)
     int64_t halo_total = 0;
     for (int p = 0; p < n_parts; ++p) {
         Part& P = plan.parts[p];

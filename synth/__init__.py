@@ -345,6 +345,49 @@ def cu_fcc_large(cells=(64, 64, 64), sigma=0.0, seed=4) -> System:
     return _fcc_system(cells, 3.615, sigma, seed, [1.0], ["Cu"], "fcc-cu-%d" % n)
 
 
+def supported_particles(cells_xy=(8, 8), slab_cells=3, radius=6.0, grid=(2, 2), a=3.6,
+                        gap=2.0, vacuum=10.0, sigma=0.05, seed=5) -> System:
+    """Spherical FCC particles on a planar FCC support slab: a heterogeneous
+    geometry like the paper's Pt-TiO2 particles on slabs (Supplementary S1).
+
+    The support (species 0, Ni) is slab_cells FCC cells thick, periodic in x
+    and y (box cells_xy * a).  One particle (species 1, Cu) of the given
+    radius sits above the centre of each of the grid[0] x grid[1] tiles of
+    the xy plane: the FCC sites, with a site at the particle centre, within
+    the radius.  Its lowest sites lie ``gap`` above the support's top atomic
+    plane; ``vacuum`` separates the particle tops from the support's periodic
+    image in z.  Coordinates get N(0, sigma^2) displacements.
+    """
+    nx, ny = cells_xy
+    slab, _ = fcc((nx, ny, slab_cells), a)
+    Lx, Ly = nx * a, ny * a
+    top = (slab_cells - 0.5) * a                 # highest support plane
+    zc = top + gap + radius
+    m = int(math.ceil(radius / a)) + 1
+    basis = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]])
+    g = np.arange(-m, m + 1, dtype=np.float64)
+    gz, gy, gx = np.meshgrid(g, g, g, indexing="ij")
+    sites = ((np.stack([gx.ravel(), gy.ravel(), gz.ravel()], axis=1)[:, None, :]
+              + basis[None]) * a).reshape(-1, 3)
+    ball = sites[np.sqrt((sites ** 2).sum(axis=1)) <= radius]
+    if 2 * radius + 2.0 > min(Lx / grid[0], Ly / grid[1]):
+        raise ValueError("particles would touch: enlarge cells_xy or reduce radius")
+    parts = []
+    for iy in range(grid[1]):
+        for ix in range(grid[0]):
+            c = np.array([(ix + 0.5) * Lx / grid[0], (iy + 0.5) * Ly / grid[1], zc])
+            parts.append(ball + c)
+    part_pos = np.concatenate(parts)
+    pos = np.concatenate([slab, part_pos])
+    box = np.array([Lx, Ly, zc + radius + vacuum], dtype=np.float64)
+    if sigma > 0:
+        pos = displace(pos, sigma, seed)
+    sp = np.concatenate([np.zeros(len(slab), np.int32), np.ones(len(part_pos), np.int32)])
+    masses = np.array([MASS["Ni"], MASS["Cu"]])[sp]
+    return System(pos, box, sp, masses, "supported-particles-%d" % len(pos),
+                  {"n_support": len(slab), "n_particle_atoms": len(part_pos)})
+
+
 def model_c1() -> ModelDesc:
     """108-atom case: S=1, F=64, lmax=1, 2 layers, r_c = 5."""
     return ModelDesc(n_species=1, F=64, lmax=1, n_layers_full=2, r_cut=5.0,

@@ -68,3 +68,23 @@ def test_rsa_liquid_min_distance():
     r = np.sqrt((d * d).sum(-1)) + np.eye(300) * 10
     assert r.min() >= 1.8
     assert abs(300 / np.prod(box) - 0.08) < 1e-12
+
+
+def test_supported_particles_geometry():
+    """Particles sit above the support with the stated gap; no two atoms
+    closer than 1.8 A; the vacuum keeps particle tops out of reach of the
+    support's periodic image."""
+    s = synth.supported_particles()
+    ns, npart = s.extra["n_support"], s.extra["n_particle_atoms"]
+    assert len(s.pos) == ns + npart and ns == 4 * 8 * 8 * 3
+    assert np.all(s.species[:ns] == 0) and np.all(s.species[ns:] == 1)
+    d = s.pos[:, None, :] - s.pos[None, :, :]
+    d -= s.box * np.round(d / s.box)
+    r = np.sqrt((d ** 2).sum(-1)) + np.eye(len(s.pos)) * 1e9
+    assert r.min() > 1.8
+    top = (3 - 0.5) * 3.6
+    assert s.pos[ns:, 2].min() > top + 2.0 - 0.5          # gap minus displacement
+    assert s.box[2] - s.pos[ns:, 2].max() + s.pos[:ns, 2].min() > 6.5 + 3.0
+    # four particles, one per xy tile
+    tiles = (s.pos[ns:, 0] >= s.box[0] / 2).astype(int) * 2 + (s.pos[ns:, 1] >= s.box[1] / 2)
+    assert np.all(np.bincount(tiles) == npart // 4)

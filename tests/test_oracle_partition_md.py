@@ -122,3 +122,61 @@ def test_local_cluster_force_equals_full_evaluation():
         Ek, Fk = op.local_energy_force(s.pos, s.species, s.box, w, d, 2, k)
         assert abs(Ek - Ei[k]) <= 1e-12 * abs(Ei[k])
         assert np.abs(Fk - F[k]).max() <= 1e-12 * max(1.0, np.abs(F[k]).max())
+
+
+def test_assignment_plan_with_slab_bins_is_the_bfs_plan():
+    """Stage 1 given as an assignment reproduces the spatial-grid BFS plan."""
+    s = synth.alloy_fcc(cells=(5, 5, 10), sigma=0.1, seed=8)
+    e = nb.edges(s.pos, s.box, 4.0)
+    bins = op.root_bins(s.pos, s.box, 4)
+    pa, Ha = op.assignment_plan(bins, e, 4, 2)
+    pb, Hb = op.plan(s.pos, s.box, e, 4, 2, 4.0, "bfs")
+    assert Ha == Hb
+    for (ra, xa), (rb, xb) in zip(pa, pb):
+        assert np.array_equal(ra, rb) and np.array_equal(xa, xb)
+
+
+def test_partitioned_equals_unpartitioned_for_any_assignment():
+    """Exactness does not depend on the shape of the root sets: a random
+    (fragmented) assignment and a supported-particle system both reproduce
+    the unpartitioned energy and forces."""
+    d, w = _small_alloy_model(2)
+    for s, assign in [
+        (synth.alloy_fcc(cells=(5, 5, 5), sigma=0.1, seed=9),
+         synth.seeded_permutation(500, 3, synth.STREAM_SPLIT) % 3),
+        (synth.supported_particles(cells_xy=(6, 6), slab_cells=2, radius=4.5, grid=(1, 1),
+                                   seed=4), None),
+    ]:
+        e = nb.edges(s.pos, s.box, d.r_cut)
+        if assign is None:   # quadrants of the xy plane
+            x = nb.wrap(s.pos, s.box)
+            assign = (2 * (x[:, 0] >= s.box[0] / 2) + (x[:, 1] >= s.box[1] / 2)).astype(int)
+        P = int(assign.max()) + 1
+        E, Ei, F = om.energy_forces(s.pos, s.species, s.box, e, w, d, 2)
+        parts, H = op.assignment_plan(assign, e, P, 2)
+        Ep, Eip, Fp = op.partitioned_energy_forces(s.pos, s.species, s.box, e, w, d, 2, parts)
+        frms = np.sqrt((F ** 2).mean())
+        assert abs(Ep - E) < 1e-12 * abs(E)
+        assert np.allclose(Eip, Ei, atol=1e-12)
+        assert np.abs(Fp - F).max() < 1e-11 * frms
+        # one hop too few breaks it (the halo depth is what exactness needs)
+        short, _ = op.assignment_plan(assign, e, P, 1)
+        _, _, Fs = op.partitioned_energy_forces(s.pos, s.species, s.box, e, w, d, 2, short)
+        assert np.abs(Fs - F).max() > 1e-6 * frms
+
+
+def test_edge_cut_and_weights_by_hand():
+    """A 4-cycle 0-1-2-3-0 split {0,1} | {2,3} cuts edges 1-2 and 3-0."""
+    und = [(0, 1), (1, 2), (2, 3), (3, 0)]
+    recv = np.array([a for a, b in und] + [b for a, b in und])
+    send = np.array([b for a, b in und] + [a for a, b in und])
+    edges = (recv, send, np.zeros(8, np.int8))
+    assert op.edge_cut([0, 0, 1, 1], edges) == 2
+    assert op.edge_cut([0, 1, 0, 1], edges) == 4
+    assert op.edge_cut([0, 0, 0, 0], edges) == 0
+    assert list(op.part_weights([0, 0, 1, 1], 3)) == [2, 2, 0]
+    # BFS halo of root {0} with one hop: its two neighbours; H = 2 / 4 per part sum
+    parts, H = op.assignment_plan(np.array([0, 1, 1, 1]), edges, 2, 1)
+    assert list(np.nonzero(parts[0][1])[0]) == [0, 1, 3]
+    assert list(np.nonzero(parts[1][1])[0]) == [0, 1, 2, 3]
+    assert H == (2 + 1) / 4
