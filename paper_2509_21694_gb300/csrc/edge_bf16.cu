@@ -569,11 +569,14 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                         hjc[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + jb + q * TF);
                     }
                 }
-#pragma unroll 2
-                for (int i = 0; i < 8; ++i) {
+                // one edge of the slice: gathers of edge i in (ajc, hjc); those of
+                // edge i + 1 are fetched into (ajn, hjn) meanwhile; the caller
+                // swaps the roles of the two buffers, so nothing is copied
+                auto edge_step = [&](int i, float (&ajc)[TNLM], float (&hjc)[TNLM],
+                                     float (&ajn)[TNLM], float (&hjn)[TNLM]) -> bool {
                     const int e = sl * 8 + i;
                     const int lr = w.row[e];
-                    if (lr < 0) break;
+                    if (lr < 0) return false;
                     float R[PP::NP], dR[PP::NP];
 #pragma unroll
                     for (int q = 0; q < PP::NP; ++q) {
@@ -694,11 +697,12 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
 #pragma unroll
                         for (int q = 0; q < 3; ++q) fs[q] += fmaf(gr, u[q], (v[q] - vu * u[q]) * ir);
                     }
-#pragma unroll
-                    for (int q = 0; q < TNLM; ++q) {
-                        ajc[q] = ajn[q];
-                        hjc[q] = hjn[q];
-                    }
+                    return true;
+                };
+#pragma unroll 1
+                for (int i = 0; i < 8; i += 2) {
+                    if (!edge_step(i, ajc, hjc, ajn, hjn)) break;
+                    if (!edge_step(i + 1, ajn, hjn, ajc, hjc)) break;
                 }
                 fold();
                 tc::fence_before_sync();
