@@ -321,6 +321,7 @@ def run_ours(args, rank, world):
                            if kind in TRAFFIC_BYTES_PER_EDGE_BF16 else None)
                 roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_edge_" + kind,
+                        "edges_per_launch": edges_per_launch,
                         "peak_note": "bf16_tflops_sustained of %s peaks" % peak_kind,
                         "flops_per_launch": flops,
                         "traffic_note": "DRAM bytes per edge from the ncu capture in "

@@ -105,6 +105,7 @@ struct Part {
     int64_t n_ext = 0, n_root = 0, n_edges = 0;
     std::vector<int64_t> n_le;   // atoms of hop class <= m, m = 0..K (prefix sizes)
     std::vector<int64_t> e_le;   // edges of the rows of those prefixes
+    std::vector<int64_t> e_same; // edges of class-m rows whose sender is also class m
     DevBuf gid;       // int32 [n_ext]  sorted-global ids
     DevBuf is_root;   // uint8 [n_ext]
     DevBuf row_ptr;   // int64 [n_ext + 1]
@@ -128,6 +129,7 @@ struct SubSys {
     const uint8_t* is_root;   // nullptr = all roots
     std::vector<int64_t> n_le; // prefix sizes of hop classes 0..K (empty = all n)
     std::vector<int64_t> e_le; // their edge counts
+    std::vector<int64_t> e_same; // per class m: edges with both ends in class m (empty = none)
 };
 
 struct Workspace {

@@ -54,6 +54,7 @@ constexpr int RPG_B = 4;           // adjoint
 constexpr int RPG = RPG_F > RPG_B ? RPG_F : RPG_B;   // row-group storage
 constexpr int SCF = 128;           // forward super-chunk: 128 edges, slices of 16
 constexpr int SCB = 64;            // adjoint super-chunk: 64 edges + 64 tangents, slices of 8 + 8
+constexpr int KWIN = 512;          // adjoint: raw edges compacted at a time (4 per thread)
 constexpr int kErrTimeout = 2;
 
 template <bool FIRST>
@@ -83,6 +84,8 @@ struct alignas(1024) WgState {
     float Y[SCF][TNLM - 1];          // Y_lm for lm = 1..8 (Y_00 = 1)
     float u[SCB][4];                 // unit vector, r
     int row[SCF], col[SCF];
+    int klist[KWIN];                 // adjoint: kept edges of a window (offsets from its start)
+    int kwarp[4];
     double fpart[RPG][4][3];         // per-row, per-warp force partial sums
     double vpart[RPG][4][9];         // per-row, per-warp virial partial sums (stress)
     int64_t rp[RPG + 1];
@@ -472,11 +475,49 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                 }
             }
         };
-        for (int64_t sc = e_beg; sc < e_end && alive; sc += SCB) {
+        // Rows >= n_recv receive no messages at this layer, so their adjoints
+        // are zero and an edge between two of them adds exact zeros to every
+        // sum: when the group holds such rows its edges are compacted, in
+        // order, into a list without those edges, a window at a time.
+        const bool compact = a.n_recv > 0 && r0 + nrows > a.n_recv;
+        for (int64_t wb = e_beg; wb < e_end && alive;) {
+          const int64_t we = compact ? min(wb + (int64_t)KWIN, e_end) : e_end;
+          int64_t nk = we - wb;
+          if (compact) {
+              int keep[4], cnt = 0;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                  const int64_t e = wb + 4 * lt + q;
+                  keep[q] = 0;
+                  if (e < we) {
+                      const int lr = find_row_t(w.rp, nrows, e);
+                      keep[q] = !(r0 + lr >= a.n_recv && (int64_t)a.col[e] >= a.n_recv);
+                  }
+                  cnt += keep[q];
+              }
+              int inc = cnt;
+#pragma unroll
+              for (int o = 1; o < 32; o <<= 1) {
+                  const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                  if (lane >= o) inc += y;
+              }
+              if (lane == 31) w.kwarp[warp & 3] = inc;
+              wg_sync(g);
+              int off = inc - cnt;
+              for (int q = 0; q < (warp & 3); ++q) off += w.kwarp[q];
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                  if (keep[q]) w.klist[off++] = 4 * lt + q;
+              nk = w.kwarp[0] + w.kwarp[1] + w.kwarp[2] + w.kwarp[3];
+              wg_sync(g);
+          }
+          for (int64_t kc = 0; kc < nk && alive; kc += SCB) {
             if (lt < SCB) {
                 float eps[kNB], deps[kNB], Y[TNLM], u4[4];
                 int col;
-                const int lr = edge_geometry<true>(a, w.rp, sc + lt, e_end, r0, nrows, eps, deps,
+                const int64_t v = kc + lt;
+                const int64_t e = v < nk ? wb + (compact ? (int64_t)w.klist[v] : v) : e_end;
+                const int lr = edge_geometry<true>(a, w.rp, e, e_end, r0, nrows, eps, deps,
                                                    Y, u4, col);
                 w.row[lt] = lr;
                 w.col[lt] = col;
@@ -715,6 +756,8 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                     tc::mma_commit(&w.mbar);
                 }
             }
+          }
+          wb = we;
         }
         if (!alive) break;
         if (cur >= 0) {

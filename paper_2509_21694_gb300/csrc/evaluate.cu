@@ -294,6 +294,11 @@ struct Prefix {
         const int kp = (int)ss.e_le.size() - 1;
         return ss.e_le[hops < 0 ? 0 : (hops > kp ? kp : hops)];
     }
+    // edges whose two ends are both in class `hops` (zero for the whole graph)
+    int64_t same(int hops) const {
+        if (ss.e_same.empty() || hops < 0 || hops >= (int)ss.e_same.size()) return 0;
+        return ss.e_same[hops];
+    }
 };
 
 int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeConst& kc, int K,
@@ -424,9 +429,15 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         ea.Gout = Gout;
         ea.Gin = t == 0 ? nullptr : Gin;
         ea.frc = b.floc;
+        // rows nrows..erows-1 (the outermost class of this layer) receive no
+        // messages at layer t, so their adjoints are zero and an edge between
+        // two of them contributes exactly nothing: the tensor-core adjoint
+        // skips those edges
+        ea.n_recv = nrows < erows ? nrows : 0;
         {
-            TimerScope ts(ctx, t == 0 ? MP_TIMER_EDGE_BWD_L0 : MP_TIMER_EDGE_BWD, pre.edges(K - t),
-                          erows);
+            const int64_t e_work = pre.edges(K - t) -
+                                   (precision == MP_BF16 && nrows < erows ? pre.same(K - t) : 0);
+            TimerScope ts(ctx, t == 0 ? MP_TIMER_EDGE_BWD_L0 : MP_TIMER_EDGE_BWD, e_work, erows);
             if (precision == MP_BF16)
                 MP_TRY(launch_edge_bwd_bf16(m, ea, st, ctx->num_sms));
             else
@@ -468,14 +479,14 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
     std::vector<SubSys> subs;
     if (!plan) {
         subs.push_back(SubSys{n, g.n_edges, g.row_ptr.as<int64_t>(), g.col.as<int32_t>(),
-                              g.shift.as<int8_t>(), nullptr, nullptr, {}, {}});
+                              g.shift.as<int8_t>(), nullptr, nullptr, {}, {}, {}});
     } else {
         for (const Part& P : plan->parts)
             if (P.n_root > 0)   // a slab without roots contributes nothing
                 subs.push_back(SubSys{P.n_ext, P.n_edges, P.row_ptr.as<int64_t>(),
                                       P.col.as<int32_t>(), P.shift.as<int8_t>(),
                                       P.gid.as<int32_t>(), P.is_root.as<uint8_t>(), P.n_le,
-                                      P.e_le});
+                                      P.e_le, P.e_same});
     }
     int64_t nmax = 0;
     for (const SubSys& s : subs) nmax = s.n > nmax ? s.n : nmax;

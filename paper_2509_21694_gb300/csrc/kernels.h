@@ -29,6 +29,10 @@ struct EdgeArgs {
     // g_e added to the row's force, component-major [9][vir_stride], accumulated
     double* vir;
     int64_t vir_stride;
+    // adjoint: rows < n_recv receive messages at this layer; an edge whose two
+    // ends are both >= n_recv has zero adjoint on both sides and may be
+    // skipped (<= 0: every row is a receiver)
+    int64_t n_recv;
 };
 
 int launch_edge_fwd_f32(const Model& m, const EdgeArgs& a, cudaStream_t st);

@@ -35,20 +35,46 @@ __device__ __forceinline__ int64_t ext_rows(const int32_t* cnt, int K) {
     return t;
 }
 
+// Hop class of local row l: rows are placed class by class.
+__device__ __forceinline__ int local_class(const int32_t* cnt, int K, int64_t l) {
+    int64_t t = 0;
+    for (int m = 0; m <= K; ++m) {
+        t += cnt[m];
+        if (l < t) return m;
+    }
+    return K + 1;
+}
+
+// Local degree of every row, and per class m the number of local edges whose
+// two ends are both of class m (esame[m], accumulated).  Every lane of a warp
+// reaches the warp-wide reductions, also past the end of the rows.
 __global__ void k_local_deg(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                             const int32_t* __restrict__ gid, const int32_t* __restrict__ g2l,
                             int64_t n, const int32_t* __restrict__ cnt, int K,
-                            int32_t* __restrict__ deg) {
-    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= n) return;
-    if (l >= ext_rows(cnt, K)) {
-        deg[l] = 0;
-        return;
+                            int32_t* __restrict__ deg, unsigned long long* __restrict__ esame) {
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n_ext = ext_rows(cnt, K);
+    int m = K + 1, c = 0, same = 0;
+    if (l < n_ext) {
+        m = local_class(cnt, K, l);
+        const int s = gid[l];
+        for (int64_t e = row_ptr[s]; e < row_ptr[s + 1]; ++e) {
+            const int t = g2l[col[e]];
+            if (t >= 0) {
+                ++c;
+                same += local_class(cnt, K, t) == m;
+            }
+        }
     }
-    int s = gid[l];
-    int c = 0;
-    for (int64_t e = row_ptr[s]; e < row_ptr[s + 1]; ++e) c += g2l[col[e]] >= 0;
-    deg[l] = c;
+    if (l < n) deg[l] = c;
+    const unsigned full = 0xffffffffu;
+    const bool uniform = __all_sync(full, m == __shfl_sync(full, m, 0));
+    if (uniform) {
+        const unsigned tot = __reduce_add_sync(full, (unsigned)same);
+        if ((threadIdx.x & 31) == 0 && tot && m <= K) atomicAdd(&esame[m], (unsigned long long)tot);
+    } else if (same && m <= K) {
+        atomicAdd(&esame[m], (unsigned long long)same);
+    }
 }
 
 __global__ void k_local_fill(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -292,7 +318,7 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
     // a partition's edges are a subset of the graph's), and the sizes come
     // back in one copy at the end.
     DevBuf& stats = ws.pstats;
-    const int ns = 2 * (K + 1);
+    const int ns = 3 * (K + 1);   // n_le, e_le, e_same per class
     // per partition: ns sizes; then one slot for the count of invalid
     // assignment entries; then the class counts
     MP_TRY(stats.reserve(sizeof(int64_t) * (n_parts * ns + 1) +
@@ -300,7 +326,7 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
     int64_t* d_stats = stats.as<int64_t>();
     int64_t* d_bad = d_stats + (size_t)n_parts * ns;
     int32_t* d_cnt = reinterpret_cast<int32_t*>(d_bad + 1);
-    MP_CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int64_t), st));
+    MP_CUDA_TRY(cudaMemsetAsync(d_stats, 0, sizeof(int64_t) * ((size_t)n_parts * ns + 1), st));
     if (d_assign) {
         k_check_assign<<<grid_for(n, 256), 256, 0, st>>>(
             d_assign, n, n_parts, reinterpret_cast<unsigned long long*>(d_bad));
@@ -347,7 +373,8 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
             note_launch();
         }
         k_local_deg<<<grid_for(n, 256), 256, 0, st>>>(
-            g.row_ptr.as<int64_t>(), g.col.as<int32_t>(), P.gid.as<int32_t>(), g2l, n, cnt, K, flag);
+            g.row_ptr.as<int64_t>(), g.col.as<int32_t>(), P.gid.as<int32_t>(), g2l, n, cnt, K, flag,
+            reinterpret_cast<unsigned long long*>(d_stats + (size_t)p * ns + 2 * (K + 1)));
         note_launch();
         MP_TRY(exclusive_scan_i64(flag, P.row_ptr.as<int64_t>(), n, ws.tmp, st));
         k_local_fill<<<grid_for(n, 256), 256, 0, st>>>(
@@ -369,6 +396,7 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
         const int64_t* h = h_stats.data() + (size_t)p * ns;
         P.n_le.assign(h, h + K + 1);
         P.e_le.assign(h + K + 1, h + 2 * (K + 1));
+        P.e_same.assign(h + 2 * (K + 1), h + 3 * (K + 1));
         P.n_root = P.n_le[0];
         P.n_ext = P.n_le[K];
         P.n_edges = P.e_le[K];
