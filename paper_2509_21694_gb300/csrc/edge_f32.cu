@@ -228,6 +228,8 @@ struct BwdSmem {
     double vrow[RPB][9];     // per-row virial sum_e g_e (x) d_e (when requested)
     int row[CB], col[CB];
     int64_t rp[RPB + 1];
+    int klist[4 * F];        // kept edges of a window of raw edges (offsets from its start)
+    int kwarp[F / 32];
 };
 
 // R (value) and dR/dr (tangent) of the radial MLP's last layer for CB edges,
@@ -313,9 +315,47 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
             a.Gin[base + q * F] = a.Gout[base + q * F] + (with_acc ? gacc[q] : 0.f);
     };
 
-    for (int64_t cb = e_beg; cb < e_end; cb += CB) {
+    // Rows >= n_recv receive no messages at this layer: their adjoints are
+    // zero and an edge between two of them adds exact zeros, so the block's
+    // edges are compacted (in order) without those edges, 4 F at a time.
+    const bool compact = a.n_recv > 0 && r0 + nrows > a.n_recv;
+    const int lane = c & 31, wid = c >> 5;
+    for (int64_t wb = e_beg; wb < e_end;) {
+      const int64_t we = compact ? min(wb + (int64_t)(4 * F), e_end) : e_end;
+      int64_t nk = we - wb;
+      if (compact) {
+          int keep[4], cnt = 0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+              const int64_t e = wb + 4 * c + q;
+              keep[q] = 0;
+              if (e < we) {
+                  const int lr = find_row(s.rp, nrows, e);
+                  keep[q] = !(r0 + lr >= a.n_recv && (int64_t)a.col[e] >= a.n_recv);
+              }
+              cnt += keep[q];
+          }
+          int inc = cnt;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+              const int y = __shfl_up_sync(0xffffffffu, inc, o);
+              if (lane >= o) inc += y;
+          }
+          if (lane == 31) s.kwarp[wid] = inc;
+          __syncthreads();
+          int off = inc - cnt;
+          for (int q = 0; q < wid; ++q) off += s.kwarp[q];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+              if (keep[q]) s.klist[off++] = 4 * c + q;
+          nk = 0;
+          for (int q = 0; q < F / 32; ++q) nk += s.kwarp[q];
+          __syncthreads();
+      }
+      for (int64_t cb = 0; cb < nk; cb += CB) {
         if (c < CB) {
-            const int64_t e = cb + c;
+            const int64_t v = cb + c;
+            const int64_t e = v < nk ? wb + (compact ? (int64_t)s.klist[v] : v) : e_end;
             float eps[kNB], deps[kNB], Y[NLM], u4[4] = {0.f, 0.f, 0.f, 1.f};
             if (e < e_end) {
                 const int lr = find_row(s.rp, nrows, e);
@@ -506,6 +546,8 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
             }
         }
         __syncthreads();
+      }
+      wb = we;
     }
     if (cur >= 0) {
         flush(cur, true);

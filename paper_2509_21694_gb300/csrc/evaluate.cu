@@ -431,12 +431,11 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         ea.frc = b.floc;
         // rows nrows..erows-1 (the outermost class of this layer) receive no
         // messages at layer t, so their adjoints are zero and an edge between
-        // two of them contributes exactly nothing: the tensor-core adjoint
-        // skips those edges
+        // two of them contributes exactly nothing: the adjoint kernels skip
+        // those edges
         ea.n_recv = nrows < erows ? nrows : 0;
         {
-            const int64_t e_work = pre.edges(K - t) -
-                                   (precision == MP_BF16 && nrows < erows ? pre.same(K - t) : 0);
+            const int64_t e_work = pre.edges(K - t) - (nrows < erows ? pre.same(K - t) : 0);
             TimerScope ts(ctx, t == 0 ? MP_TIMER_EDGE_BWD_L0 : MP_TIMER_EDGE_BWD, e_work, erows);
             if (precision == MP_BF16)
                 MP_TRY(launch_edge_bwd_bf16(m, ea, st, ctx->num_sms));
