@@ -88,13 +88,14 @@ def _t(a):
 
 
 def atom_energies(pos_t, species, box, recv, send, code, w, desc, n_layers,
-                  use_head=False, collect=None, strain=None):
+                  use_head=False, collect=None, strain=None, layer_masks=None):
     """Per-atom energies E_i (torch float64 [N]) as a differentiable function
     of pos_t; recv/send/code is the edge list of these positions.  With
     ``strain`` (a 3 x 3 tensor eps) every edge vector is deformed as
     d -> (I + eps) d, which is what a homogeneous strain of positions and box
     does to it (the edge set itself does not change under an infinitesimal
-    strain)."""
+    strain).  With ``layer_masks`` (one boolean array over the edges per
+    layer) layer t sums messages over the edges of mask t only."""
     F, lmax = desc.F, desc.lmax
     N = pos_t.shape[0]
     recv_t = torch.as_tensor(recv, dtype=torch.long)
@@ -118,6 +119,8 @@ def atom_energies(pos_t, species, box, recv, send, code, w, desc, n_layers,
     for t in range(n_layers):
         W1, W2, W3 = _t(w["W1"][t]), _t(w["W2"][t]), _t(w["W3"][t])
         R = silu(silu(eps @ W1.T) @ W2.T) @ W3.T
+        if layer_masks is not None:
+            R = R * _t(np.asarray(layer_masks[t], dtype=np.float64))[:, None]
         h0j = h0[send_t]
         A0 = torch.zeros(N, F, dtype=_T).index_add(0, recv_t, R[:, :F] * h0j) / desc.n_avg
         s = A0 @ _t(w["W0"][t]).T + _t(w["b"][t])
@@ -150,7 +153,7 @@ def head_energy(h0, w):
 
 
 def energy_forces(pos, species, box, edges, w, desc, n_layers, seed_mask=None,
-                  use_head=False):
+                  use_head=False, layer_masks=None):
     """(E, E_i, F) in float64 numpy.
 
     E = sum_i s_i E_i with s_i = seed_mask (1 for all atoms by default);
@@ -162,7 +165,7 @@ def energy_forces(pos, species, box, edges, w, desc, n_layers, seed_mask=None,
     pos_t = torch.tensor(pos_w, dtype=_T, requires_grad=True)
     recv, send, code = edges
     Ei = atom_energies(pos_t, species, box, recv, send, code, w, desc, n_layers,
-                       use_head=use_head)
+                       use_head=use_head, layer_masks=layer_masks)
     if seed_mask is None:
         E = Ei.sum()
     else:

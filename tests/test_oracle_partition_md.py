@@ -180,3 +180,46 @@ def test_edge_cut_and_weights_by_hand():
     assert list(np.nonzero(parts[0][1])[0]) == [0, 1, 3]
     assert list(np.nonzero(parts[1][1])[0]) == [0, 1, 2, 3]
     assert H == (2 + 1) / 4
+
+
+def test_per_layer_receiver_edges_suffice():
+    """Inside one partition, layer t only needs the edges whose receiver lies
+    within K-1-t hops of a root: restricting every layer to those edges
+    leaves the root energies and all forces unchanged.  In particular an
+    edge whose two ends are both exactly K-t hops out is used at no layer
+    >= t, in neither direction, so it contributes nothing to the adjoint of
+    layer t (the edges the GPU adjoint skips); and a receiver set one hop
+    smaller changes the result."""
+    s = synth.alloy_fcc(cells=(5, 5, 10), sigma=0.1, seed=8)
+    d, w = _small_alloy_model(3)
+    e = nb.edges(s.pos, s.box, d.r_cut)
+    recv, send, code = e
+    K = 2
+    roots = op.root_bins(s.pos, s.box, 4) == 1
+    level = np.full(len(s.pos), K + 1)
+    level[roots] = 0
+    for h in range(1, K + 1):      # BFS levels over the symmetric edge set
+        reach = np.zeros(len(s.pos), bool)
+        reach[recv[level[send] < h]] = True
+        level[(level > K) & reach] = h
+    ext = level <= K
+    gid = np.nonzero(ext)[0]
+    lr, ls, lc = op.sub_edges(e, ext)
+    lev = level[gid]
+    seed = roots[gid].astype(np.float64)
+    args = (s.pos[gid], s.species[gid], s.box, (lr, ls, lc), w, d, K)
+    E0, Ei0, F0 = om.energy_forces(*args, seed_mask=seed)
+    masks = [lev[lr] <= K - 1 - t for t in range(K)]
+    E1, Ei1, F1 = om.energy_forces(*args, seed_mask=seed, layer_masks=masks)
+    frms = np.sqrt((F0 ** 2).mean())
+    assert abs(E1 - E0) < 1e-12 * abs(E0)
+    assert np.abs(F1 - F0).max() < 1e-11 * frms
+    # the edges dropped at layer t include every edge between two atoms of
+    # level K - t, in both directions
+    for t in range(K):
+        outer = (lev[lr] == K - t) & (lev[ls] == K - t)
+        assert outer.any() and not np.any(masks[t] & outer)
+    # one level too few at the first layer is not enough
+    short = [lev[lr] <= K - 2 - t for t in range(K)]
+    _, _, F2 = om.energy_forces(*args, seed_mask=seed, layer_masks=short)
+    assert np.abs(F2 - F0).max() > 1e-6 * frms
