@@ -325,14 +325,19 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
 #pragma unroll
                     for (int q = 0; q < TNLM; ++q) hjn[q] = (FIRST && q > 0) ? 0.f : __ldg(hq + q * TF);
                 }
+                float Rb[PP::NP][8];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int e = sl * 16 + i;
                     const int lr = w.row[e];
                     if (lr < 0) break;
+                    if ((i & 7) == 0) {   // radial outputs of 8 edges per path at once
+#pragma unroll
+                        for (int q = 0; q < PP::NP; ++q) tc::tmem_ld8(tl + 16 * q + i, Rb[q]);
+                    }
                     float R[PP::NP];
 #pragma unroll
-                    for (int q = 0; q < PP::NP; ++q) tc::tmem_ld1(tl + 16 * q + i, R[q]);
+                    for (int q = 0; q < PP::NP; ++q) R[q] = Rb[q][i & 7];
                     if (i + 2 < 16) {
                         const float* __restrict__ hp = Hin + ((int64_t)w.col[e + 2] * TNLM) * TF + c;
 #pragma unroll
