@@ -113,3 +113,26 @@ def test_slabs_without_roots(mp, precision):
     assert np.abs(F1 - F0).max() <= 1e-6 * np.sqrt((F0 ** 2).mean())
     assert np.array_equal(e0.cpu().numpy(), e1.cpu().numpy())
     pot.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_partitioned_equals_unpartitioned_three_layers(mp, precision):
+    """K = 3: the adjoint of every layer (outermost classes 3, 2 and 1)
+    skips the edges between two atoms of its outermost class, and the
+    partitioned forces still equal the unpartitioned ones."""
+    s = synth.alloy_fcc(cells=(6, 6, 16), sigma=0.1, seed=9)
+    d = synth.model_alloy(n_layers_full=3)
+    d.rep_eps = 0.3
+    w = synth.make_weights(d, 1)
+    prec = mp.MP_FP32 if precision == "fp32" else mp.MP_BF16
+    pot, pos, sp = _setup(mp, s, d, w)
+    E0, F0, e0 = pot.energy_forces(pos, sp, s.box, 3, precision=prec, per_atom=True)
+    for mode in (0, 1):
+        E1, F1, e1 = pot.energy_forces(pos, sp, s.box, 3, precision=prec, n_parts=4,
+                                       halo_mode=mode, per_atom=True)
+        a = F0.cpu().numpy().astype(np.float64)
+        b = F1.cpu().numpy().astype(np.float64)
+        frms = np.sqrt((a ** 2).mean())
+        assert np.abs(b - a).max() <= 1e-6 * frms, np.abs(b - a).max() / frms
+        assert np.array_equal(e0.cpu().numpy(), e1.cpu().numpy())
+    pot.close()
