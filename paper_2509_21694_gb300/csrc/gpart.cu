@@ -557,6 +557,9 @@ int graph_partition(mp_ctx* ctx, const Graph& g, int k, double imbalance, uint64
 
     // scratch sized for level 0
     DevBuf bmatch, bprop, bflag, bpre, blead, bdsz, boff, bucnt, bscol, bsw, bsmall;
+    DevBuf bdest, bgain, bdest2, bgain2;
+    BufGuard guard{&bmatch, &bprop, &bflag, &bpre, &blead, &bdsz, &boff, &bucnt, &bscol, &bsw,
+                   &bsmall, &bdest, &bgain, &bdest2, &bgain2};
     MP_TRY(bmatch.reserve(sizeof(int32_t) * (n0 + 1)));
     MP_TRY(bprop.reserve(sizeof(int32_t) * (n0 + 1)));
     MP_TRY(bflag.reserve(sizeof(int32_t) * (n0 + 1)));
@@ -571,9 +574,6 @@ int graph_partition(mp_ctx* ctx, const Graph& g, int k, double imbalance, uint64
     const size_t small_bytes = 64 + sizeof(unsigned long long) * (2 * kMaxParts * kBuckets + kMaxParts + 4) +
                                sizeof(int64_t) * 2 * kMaxParts + sizeof(int32_t) * 2 * kMaxParts;
     MP_TRY(bsmall.reserve(small_bytes));
-    DevBuf bdest, bgain, bdest2, bgain2;
-    BufGuard guard{&bmatch, &bprop, &bflag, &bpre, &blead, &bdsz, &boff, &bucnt, &bscol, &bsw,
-                   &bsmall, &bdest, &bgain, &bdest2, &bgain2};
     int* d_dmax = bsmall.as<int>();
     unsigned long long* d_cnt = reinterpret_cast<unsigned long long*>(bsmall.as<char>() + 64);
     unsigned long long* d_hin = d_cnt + 4;

@@ -273,6 +273,12 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
     plan.k_hops = k_hops;
     plan.mode = mode;
     plan.n = n;
+    // a plan rebuilt with fewer partitions frees the buffers of the extra ones
+    for (size_t q = (size_t)n_parts; q < plan.parts.size(); ++q) {
+        Part& X = plan.parts[q];
+        DevBuf* bufs[] = {&X.gid, &X.is_root, &X.row_ptr, &X.col, &X.shift};
+        for (DevBuf* b : bufs) b->release();
+    }
     plan.parts.resize(n_parts);
     Workspace& ws = ctx->ws;
     TimerScope ts(ctx, MP_TIMER_PARTITION, 0, n);
