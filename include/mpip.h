@@ -158,12 +158,13 @@ int mp_partition_assign(mp_ctx* ctx, const mp_graph* g, const int32_t* d_part, i
  * METIS-like partitioner for nanoparticles on supports and other
  * heterogeneous geometries, where uniform bins give unbalanced or
  * fragmented subgraphs; Supplementary S1 compares its halo growth factor
- * with the spatial grid's).  Minimises the number of cut edges subject to
- * every part's atom count <= max(ceil(N / n_parts),
+ * with the spatial grid's).  Heuristically minimises the number of cut
+ * edges; every part's atom count is guaranteed <= max(ceil(N / n_parts),
  * floor((1 + imbalance) N / n_parts)).  Coarsening (heavy-edge matching and
  * contraction) and k-way boundary refinement run on the GPU; the coarsest
  * graph (at most max(1024, 128 n_parts) vertices unless matching stalls) is
- * split on the host by recursive greedy bisection.  The result is a
+ * split on the host by recursive greedy bisection, and a residual excess
+ * on the atom graph is moved on the host, exactly.  The result is a
  * function of the graph and the seed only.
  *   n_parts       1..64, <= N.   imbalance  >= 0 (e.g. 0.03).
  *   d_part        [n] int32 device, written, caller's atom order.

@@ -751,6 +751,65 @@ int graph_partition(mp_ctx* ctx, const Graph& g, int k, double imbalance, uint64
         note_launch();
         MP_TRY(refine(f));
     }
+    // Exact balance on the atom graph: if a part is still above the bound,
+    // its vertices with the best admissible moves (largest gain, then
+    // smallest index) move on the host, exactly as many as the excess, to
+    // parts with room; vertices without a neighbouring part that has room
+    // move, in index order, to the part with the most room.  Total room is
+    // at least the total excess, so this ends balanced.
+    {
+        Level& L = lv[0];
+        MP_TRY(weights(L));
+        std::vector<int64_t> h_over(k);
+        MP_CUDA_TRY(cudaMemcpyAsync(h_over.data(), d_over, sizeof(int64_t) * k,
+                                    cudaMemcpyDeviceToHost, st));
+        MP_CUDA_TRY(cudaStreamSynchronize(st));
+        if (*std::max_element(h_over.begin(), h_over.end()) > 0) {
+            int32_t* dest = bdest.as<int32_t>();
+            int32_t* gain = bgain.as<int32_t>();
+            k_select<<<grid_for(L.n, 256), 256, 0, st>>>(L.rp, L.col, L.ew, L.vw, L.n,
+                                                         L.part.as<int32_t>(), d_room, d_over, 1,
+                                                         dest, gain);
+            note_launch();
+            std::vector<int32_t> h_part(L.n), h_dest(L.n), h_gain(L.n);
+            MP_CUDA_TRY(cudaMemcpyAsync(h_part.data(), L.part.as<int32_t>(),
+                                        sizeof(int32_t) * L.n, cudaMemcpyDeviceToHost, st));
+            MP_CUDA_TRY(cudaMemcpyAsync(h_dest.data(), dest, sizeof(int32_t) * L.n,
+                                        cudaMemcpyDeviceToHost, st));
+            MP_CUDA_TRY(cudaMemcpyAsync(h_gain.data(), gain, sizeof(int32_t) * L.n,
+                                        cudaMemcpyDeviceToHost, st));
+            MP_CUDA_TRY(cudaStreamSynchronize(st));
+            std::vector<int64_t> room(k);
+            for (int q = 0; q < k; ++q) room[q] = -h_over[q];   // unit vertex weights at level 0
+            std::vector<std::pair<int64_t, int>> cand;          // (-gain, vertex)
+            for (int u = 0; u < L.n; ++u)
+                if (h_over[h_part[u]] > 0 && h_dest[u] >= 0) cand.push_back({-(int64_t)h_gain[u], u});
+            std::sort(cand.begin(), cand.end());
+            for (const auto& cu : cand) {
+                const int u = cu.second, p = h_part[u], q = h_dest[u];
+                if (h_over[p] <= 0 || room[q] <= 0) continue;
+                h_part[u] = q;
+                --h_over[p];
+                ++h_over[q];
+                --room[q];
+                ++room[p];
+            }
+            for (int u = 0; u < L.n; ++u) {
+                const int p = h_part[u];
+                if (h_over[p] <= 0) continue;
+                const int q = (int)(std::max_element(room.begin(), room.end()) - room.begin());
+                if (room[q] <= 0 || q == p) break;   // cannot happen: total room >= excess
+                h_part[u] = q;
+                --h_over[p];
+                ++h_over[q];
+                --room[q];
+                ++room[p];
+            }
+            MP_CUDA_TRY(cudaMemcpyAsync(L.part.as<int32_t>(), h_part.data(),
+                                        sizeof(int32_t) * L.n, cudaMemcpyHostToDevice, st));
+            MP_CUDA_TRY(cudaStreamSynchronize(st));   // the host copy goes out of scope
+        }
+    }
     const int32_t* part0 = lv[0].part.as<int32_t>();
     k_scatter_out<<<grid_for(n0, 256), 256, 0, st>>>(n0, g.perm.as<int32_t>(), part0, d_out);
     note_launch();

@@ -243,3 +243,30 @@ def test_md_with_graph_parts_matches_unpartitioned(mp):
     dp -= s.box * np.round(dp / s.box)
     assert np.abs(dp).max() < 1e-7
     assert np.abs(out[0][1] - out[1][1]).max() < 1e-7 * np.abs(out[0][1][:, 0]).max()
+
+
+@pytest.mark.parametrize("which,k", [("particles", 2), ("liquid", 5), ("gas", 3), ("gas", 8)])
+def test_graph_partition_exact_balance(mp, which, k):
+    """With imbalance 0 every part holds at most ceil(N / k) atoms (the
+    final exact balancing step), also for a sparse gas whose graph is
+    mostly isolated atoms."""
+    if which == "particles":
+        s = synth.supported_particles(cells_xy=(14, 14), slab_cells=3, radius=8.0, seed=6)
+    elif which == "liquid":
+        s = synth.liquid3(n=2000, seed=2)
+    else:
+        pos, box = synth.rsa_liquid(3000, 0.002, 1.8, 5)
+        s = synth.System(pos, box, np.zeros(3000, np.int32), np.ones(3000))
+    d, w = _small_model()
+    n = len(s.pos)
+    e = onb.edges(s.pos, s.box, d.r_cut)
+    pot, pos, g = _graph(mp, s, d, w)
+    try:
+        part, cut = mp.mp_graph_partition(pot.ctx, g, k, 0.0, seed=1)
+        a = part.cpu().numpy()
+        wts = op.part_weights(a, k)
+        assert wts.max() <= math.ceil(n / k), wts
+        assert cut == op.edge_cut(a, e)
+    finally:
+        mp.mp_graph_free(g)
+        pot.close()
