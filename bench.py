@@ -9,6 +9,7 @@ partitions, energy + forces through the hand-written adjoint, Verlet update.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision bf16|fp32] [--layers K] [--parts P] [--cells n]
+                  [--partitioner slabs|graph] [--study partition]
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (a 6x6x6-cell block of the same lattice and model) on the host cores.
@@ -47,6 +48,9 @@ def parse():
     ap.add_argument("--structure", default="fcc", choices=["fcc", "liquid"],
                     help="fcc: FCC Cu (cells^3 x 4 atoms); liquid: 3-species random liquid")
     ap.add_argument("--atoms", type=int, default=32000, help="atoms of the liquid")
+    ap.add_argument("--partitioner", default="slabs", choices=["slabs", "graph"],
+                    help="slabs: z bins with a geometric halo (the benchmark's); graph: roots "
+                         "from the multilevel graph partitioner, assigned once, BFS halos")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--study", default=None, choices=["partition"],
@@ -136,7 +140,9 @@ def config_dict(args, n_atoms):
         "fcc-cu-%d-md-600K" % n_atoms
     return {"workload": name, "atoms": n_atoms,
             "layers_K": args.layers, "layers_full": 6, "F": 128, "lmax": 2, "r_cut_A": 6.0,
-            "partitions": args.parts, "halo_A": 6.0 * args.layers, "halo_mode": "geometric",
+            "partitions": args.parts, "halo_A": 6.0 * args.layers,
+            "halo_mode": "geometric" if args.partitioner == "slabs" else "bfs",
+            "partitioner": "z-slabs" if args.partitioner == "slabs" else "graph (multilevel)",
             "dt_fs": 1.0, "precision": args.precision,
             "l2": "inputs larger than L2 (per-partition features >> 129 MB)"}
 
@@ -231,6 +237,13 @@ def run_ours(args, rank, world):
     sp = torch.tensor(s.species, device=dev)
     md = dict(n_layers=args.layers, precision=prec, n_parts=args.parts, k_hops=args.layers,
               halo_mode=mp.MP_HALO_GEOM)
+    if args.partitioner == "graph" and args.parts > 1:
+        # roots assigned once by atom id from the initial graph; the BFS halo
+        # is rebuilt every step, so every step stays exact
+        g0 = mp.mp_build_neighbors(ctx, pos, s.box)
+        part, _ = mp.mp_graph_partition(ctx, g0, args.parts, 0.03, seed=1)
+        mp.mp_graph_free(g0)
+        md.update(halo_mode=mp.MP_HALO_BFS, part=part)
 
     # warm-up (also computes the initial forces)
     mp.mp_md_step(ctx, pos, vel, frc, mass, sp, s.box, 1.0, args.warmup, **md)
