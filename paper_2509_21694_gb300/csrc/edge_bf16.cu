@@ -671,6 +671,29 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                         Y[1] = y0.x; Y[2] = y0.y; Y[3] = y0.z; Y[4] = y0.w;
                         Y[5] = y1.x; Y[6] = y1.y; Y[7] = y1.z; Y[8] = y1.w;
                     }
+                    const float hj0 = hjc[0], hk0 = hk[0];
+                    float gr, gy[TNLM];
+                    gy[0] = 0.f;
+                    if (FIRST) {
+                        // layer 0 (no l >= 1 inputs): P_lm = hj0 ak_lm -+ hk0 aj_lm enters
+                        // both the radial term (through P_l . Y_l) and dE/dY (R_la P_lm)
+                        float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) {
+                            const float P = fmaf(hj0, ak[1 + m], -hk0 * ajc[1 + m]);
+                            s1 = fmaf(P, Y[1 + m], s1);
+                            gy[1 + m] = R[PP::sla(1)] * P;
+                        }
+#pragma unroll
+                        for (int m = 0; m < 5; ++m) {
+                            const float P = fmaf(hj0, ak[4 + m], hk0 * ajc[4 + m]);
+                            s2 = fmaf(P, Y[4 + m], s2);
+                            gy[4 + m] = R[PP::sla(2)] * P;
+                        }
+                        gr = fmaf(ak[0], hj0, ajc[0] * hk0) * dR[0];
+                        gr = fmaf(s1, dR[PP::sla(1)], gr);
+                        gr = fmaf(s2, dR[PP::sla(2)], gr);
+                    } else {
                     // Y-weighted sums of the sender's (j) and receiver's (k) alpha
                     float sj1 = 0.f, sk1 = 0.f, sj2 = 0.f, sk2 = 0.f;
 #pragma unroll
@@ -683,7 +706,7 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                         sj2 = fmaf(ajc[4 + m], Y[4 + m], sj2);
                         sk2 = fmaf(ak[4 + m], Y[4 + m], sk2);
                     }
-                    if (!FIRST) {   // dE/dh_k as the sender of the reverse edge (i <- k)
+                    {   // dE/dh_k as the sender of the reverse edge (i <- k)
                         float g0 = R[0] * ajc[0];
                         g0 = fmaf(-R[PP::sla(1)], sj1, g0);
                         g0 = fmaf(R[PP::sla(2)], sj2, g0);
@@ -696,11 +719,10 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                     // this channel's share of dE_pair/dd: radial part along u (both
                     // directions' dE/dR contracted with dR/dr) and the angular part
                     // through dE/dY; the l = 1 term of the reverse edge changes sign
-                    const float hj0 = hjc[0], hk0 = hk[0];
-                    float gr = fmaf(ak[0], hj0, ajc[0] * hk0) * dR[0];
+                    gr = fmaf(ak[0], hj0, ajc[0] * hk0) * dR[0];
                     gr = fmaf(fmaf(hj0, sk1, -hk0 * sj1), dR[PP::sla(1)], gr);
                     gr = fmaf(fmaf(hj0, sk2, hk0 * sj2), dR[PP::sla(2)], gr);
-                    if (!FIRST) {
+                    {
                         float g1b = 0.f, g2b = 0.f;
 #pragma unroll
                         for (int m = 0; m < 3; ++m)
@@ -711,8 +733,6 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                         gr = fmaf(g1b, dR[PP::slb(1)], gr);
                         gr = fmaf(g2b, dR[PP::slb(2)], gr);
                     }
-                    float gy[TNLM];
-                    gy[0] = 0.f;
                     {
                         const float a1 = R[PP::sla(1)] * hj0, b1 = R[PP::sla(1)] * hk0;
                         const float a2 = R[PP::sla(2)] * hj0, b2 = R[PP::sla(2)] * hk0;
@@ -721,6 +741,7 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
 #pragma unroll
                         for (int m = 0; m < 5; ++m) gy[4 + m] = fmaf(ak[4 + m], a2, ajc[4 + m] * b2);
                     }
+                    }
                     const float4 ue = *reinterpret_cast<const float4*>(&w.u[e][0]);
                     const float u[3] = {ue.x, ue.y, ue.z};
                     const float ir = ue.w;
@@ -728,20 +749,24 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                     sph_grad<TLMAX, float>(u, gy, v);
                     const float vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
                     if (STRESS) {
+                        // the force share is accumulated exactly as without the
+                        // stress (same operations), gq only feeds the virial
+                        const float t = fmaf(-ir, vu, gr);
                         float gq[3];
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
-                            gq[q] = fmaf(gr, u[q], (v[q] - vu * u[q]) * ir);
-                            fs[q] += gq[q];
+                            fs[q] = fmaf(t, u[q], fmaf(ir, v[q], fs[q]));
+                            gq[q] = fmaf(t, u[q], ir * v[q]);
                         }
                         const float r = 1.f / ir;
 #pragma unroll
                         for (int p = 0; p < 3; ++p)
 #pragma unroll
                             for (int q = 0; q < 3; ++q) va[3 * p + q] = fmaf(gq[p], u[q] * r, va[3 * p + q]);
-                    } else {
+                    } else {   // gr u + (v - (v . u) u) / r, regrouped
+                        const float t = fmaf(-ir, vu, gr);
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) fs[q] += fmaf(gr, u[q], (v[q] - vu * u[q]) * ir);
+                        for (int q = 0; q < 3; ++q) fs[q] = fmaf(t, u[q], fmaf(ir, v[q], fs[q]));
                     }
                     return true;
                 };
