@@ -40,6 +40,8 @@ def _check_bf16(got, ref, n):
     rmse = np.sqrt(((F - Fr) ** 2).mean())
     assert rmse <= BF16_FORCE_RMSE * frms, rmse / frms
     erms = np.sqrt((Eir ** 2).mean())
+    print("BF16 vs oracle: force RMSE %.3g F_rms, max %.3g F_rms, energy %.3g"
+          % (rmse / frms, np.abs(F - Fr).max() / frms, abs(E - Er) / (n * erms)))
     assert abs(E - Er) <= BF16_ENERGY * n * erms, abs(E - Er) / (n * erms)
     return rmse / frms
 
