@@ -64,7 +64,7 @@ def parse():
 # averaged over its layer-0 and layer-1 launches, from one ncu capture on
 # 131,072 atoms (profiles/edge_node_kernels_bf16_131k.md); scaled by the
 # edges of a launch.  Must be re-measured whenever that kernel changes.
-TRAFFIC_BYTES_PER_EDGE_BF16 = {"bwd": 438.0}
+TRAFFIC_BYTES_PER_EDGE_BF16 = {"bwd": 436.0}
 
 
 def max_over_ranks(ms, world, dev):
