@@ -540,6 +540,12 @@ int graph_partition(mp_ctx* ctx, const Graph& g, int k, double imbalance, uint64
         return MP_ERR_ARG;
     cudaStream_t st = ctx->stream;
     const int n0 = (int)g.n;
+    if (k == 1) {   // one part: every atom in part 0, nothing cut
+        MP_CUDA_TRY(cudaMemsetAsync(d_out, 0, sizeof(int32_t) * n0, st));
+        MP_CUDA_TRY(cudaStreamSynchronize(st));
+        if (cut_out) *cut_out = 0;
+        return MP_OK;
+    }
     const int64_t W = n0;
     int64_t maxw = (int64_t)std::floor((1.0 + imbalance) * (double)W / k);
     maxw = std::max<int64_t>(maxw, (W + k - 1) / k);
