@@ -321,7 +321,15 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
                 if (!wg_wait(w, phase, g)) { alive = false; break; }
                 // prefetch the first edge's sender features
                 float hjc[TNLM], hjn[TNLM], hjm[TNLM];
-                {
+                // layer 0 gathers one value per edge (h0 of the sender): all 16 of
+                // the slice are requested at once, so their latency overlaps
+                float hb[FIRST ? 16 : 1];
+                if (FIRST) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        hb[i] = __ldg(Hin + ((int64_t)w.col[sl * 16 + i] * TNLM) * TF + c);
+                }
+                if (!FIRST) {
                     const int e0 = sl * 16;
                     const float* __restrict__ hp = Hin + ((int64_t)w.col[e0] * TNLM) * TF + c;
 #pragma unroll
@@ -343,10 +351,10 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
                     float R[PP::NP];
 #pragma unroll
                     for (int q = 0; q < PP::NP; ++q) R[q] = Rb[q][i & 7];
-                    if (i + 2 < 16) {
+                    if (!FIRST && i + 2 < 16) {
                         const float* __restrict__ hp = Hin + ((int64_t)w.col[e + 2] * TNLM) * TF + c;
 #pragma unroll
-                        for (int q = 0; q < TNLM; ++q) hjm[q] = (FIRST && q > 0) ? 0.f : __ldg(hp + q * TF);
+                        for (int q = 0; q < TNLM; ++q) hjm[q] = __ldg(hp + q * TF);
                     }
                     if (lr != cur) {
                         if (cur >= 0) {
@@ -360,7 +368,7 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
                         for (int q = 0; q < TNLM; ++q) acc[q] = 0.f;
                     }
                     tc::tmem_wait_ld();
-                    const float h0 = hjc[0];
+                    const float h0 = FIRST ? hb[FIRST ? i : 0] : hjc[0];
                     acc[0] = fmaf(R[0], h0, acc[0]);
                     const float t1 = R[PP::sla(1)] * h0;
 #pragma unroll
