@@ -499,308 +499,308 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
         // order, into a list without those edges, a window at a time.
         const bool compact = a.n_recv > 0 && r0 + nrows > a.n_recv;
         for (int64_t wb = e_beg; wb < e_end && alive;) {
-          const int64_t we = compact ? min(wb + (int64_t)KWIN, e_end) : e_end;
-          int64_t nk = we - wb;
-          if (compact) {
-              int keep[4], cnt = 0;
+            const int64_t we = compact ? min(wb + (int64_t)KWIN, e_end) : e_end;
+            int64_t nk = we - wb;
+            if (compact) {
+                int keep[4], cnt = 0;
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                  const int64_t e = wb + 4 * lt + q;
-                  keep[q] = 0;
-                  if (e < we) {
-                      const int lr = find_row_t(w.rp, nrows, e);
-                      keep[q] = !(r0 + lr >= a.n_recv && (int64_t)a.col[e] >= a.n_recv);
-                  }
-                  cnt += keep[q];
-              }
-              int inc = cnt;
-#pragma unroll
-              for (int o = 1; o < 32; o <<= 1) {
-                  const int y = __shfl_up_sync(0xffffffffu, inc, o);
-                  if (lane >= o) inc += y;
-              }
-              if (lane == 31) w.kwarp[warp & 3] = inc;
-              wg_sync(g);
-              int off = inc - cnt;
-              for (int q = 0; q < (warp & 3); ++q) off += w.kwarp[q];
-#pragma unroll
-              for (int q = 0; q < 4; ++q)
-                  if (keep[q]) w.klist[off++] = 4 * lt + q;
-              nk = w.kwarp[0] + w.kwarp[1] + w.kwarp[2] + w.kwarp[3];
-              wg_sync(g);
-          }
-          for (int64_t kc = 0; kc < nk && alive; kc += SCB) {
-            if (lt < SCB) {
-                float eps[kNB], deps[kNB], Y[TNLM], u4[4];
-                int col;
-                const int64_t v = kc + lt;
-                const int64_t e = v < nk ? wb + (compact ? (int64_t)w.klist[v] : v) : e_end;
-                const int lr = edge_geometry<true>(a, w.rp, e, e_end, r0, nrows, eps, deps,
-                                                   Y, u4, col);
-                w.row[lt] = lr;
-                w.col[lt] = col;
-#pragma unroll
-                for (int q = 0; q < kNB; ++q) {
-                    w.eps[lt][q] = eps[q];
-                    w.deps[lt][q] = deps[q];
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t e = wb + 4 * lt + q;
+                    keep[q] = 0;
+                    if (e < we) {
+                        const int lr = find_row_t(w.rp, nrows, e);
+                        keep[q] = !(r0 + lr >= a.n_recv && (int64_t)a.col[e] >= a.n_recv);
+                    }
+                    cnt += keep[q];
                 }
+                int inc = cnt;
 #pragma unroll
-                for (int q = 1; q < TNLM; ++q) w.Y[lt][q - 1] = Y[q];
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                if (lane == 31) w.kwarp[warp & 3] = inc;
+                wg_sync(g);
+                int off = inc - cnt;
+                for (int q = 0; q < (warp & 3); ++q) off += w.kwarp[q];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) w.u[lt][q] = u4[q];
+                for (int q = 0; q < 4; ++q)
+                    if (keep[q]) w.klist[off++] = 4 * lt + q;
+                nk = w.kwarp[0] + w.kwarp[1] + w.kwarp[2] + w.kwarp[3];
+                wg_sync(g);
             }
-            wg_sync(g);
-            {   // tile rows 2 e (a1 of edge e) and 2 e + 1 (its r-tangent): each lane of
-                // the pair forms z1 and dz1 for half of the hidden units, evaluates
-                // both rows' activations there and swaps the half its partner needs
-                const int e = lt >> 1, t = lt & 1;
-                float src[kNB], dsrc[kNB];
+            for (int64_t kc = 0; kc < nk && alive; kc += SCB) {
+                if (lt < SCB) {
+                    float eps[kNB], deps[kNB], Y[TNLM], u4[4];
+                    int col;
+                    const int64_t v = kc + lt;
+                    const int64_t e = v < nk ? wb + (compact ? (int64_t)w.klist[v] : v) : e_end;
+                    const int lr = edge_geometry<true>(a, w.rp, e, e_end, r0, nrows, eps, deps,
+                                                       Y, u4, col);
+                    w.row[lt] = lr;
+                    w.col[lt] = col;
 #pragma unroll
-                for (int b = 0; b < kNB; ++b) {
-                    src[b] = w.eps[e][b];
-                    dsrc[b] = w.deps[e][b];
+                    for (int q = 0; q < kNB; ++q) {
+                        w.eps[lt][q] = eps[q];
+                        w.deps[lt][q] = deps[q];
+                    }
+#pragma unroll
+                    for (int q = 1; q < TNLM; ++q) w.Y[lt][q - 1] = Y[q];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) w.u[lt][q] = u4[q];
                 }
+                wg_sync(g);
+                {   // tile rows 2 e (a1 of edge e) and 2 e + 1 (its r-tangent): each lane of
+                    // the pair forms z1 and dz1 for half of the hidden units, evaluates
+                    // both rows' activations there and swaps the half its partner needs
+                    const int e = lt >> 1, t = lt & 1;
+                    float src[kNB], dsrc[kNB];
+#pragma unroll
+                    for (int b = 0; b < kNB; ++b) {
+                        src[b] = w.eps[e][b];
+                        dsrc[b] = w.deps[e][b];
+                    }
 #pragma unroll 1
-                for (int j = 0; j < 4; ++j) {
-                    float keep[8], give[8];
+                    for (int j = 0; j < 4; ++j) {
+                        float keep[8], give[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float* wr = s.t.W1 + w1_row(32 * t + 8 * j + q);
-                        float z = 0.f, dz = 0.f;
+                        for (int q = 0; q < 8; ++q) {
+                            const float* wr = s.t.W1 + w1_row(32 * t + 8 * j + q);
+                            float z = 0.f, dz = 0.f;
 #pragma unroll
-                        for (int b = 0; b < kNB; ++b) {
-                            z = fmaf(wr[b], src[b], z);
-                            dz = fmaf(wr[b], dsrc[b], dz);
+                            for (int b = 0; b < kNB; ++b) {
+                                z = fmaf(wr[b], src[b], z);
+                                dz = fmaf(wr[b], dsrc[b], dz);
+                            }
+                            const float sg = sigmoid_fast(z);
+                            const float val = z * sg;
+                            const float tan = sg * fmaf(z, 1.f - sg, 1.f) * dz;
+                            keep[q] = t ? tan : val;
+                            give[q] = t ? val : tan;
                         }
-                        const float sg = sigmoid_fast(z);
-                        const float val = z * sg;
-                        const float tan = sg * fmaf(z, 1.f - sg, 1.f) * dz;
-                        keep[q] = t ? tan : val;
-                        give[q] = t ? val : tan;
-                    }
-                    float got[8];
+                        float got[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) got[q] = __shfl_xor_sync(0xffffffffu, give[q], 1);
-                    st_row_chunk(w.B, lt, 4 * t + j, keep);
-                    st_row_chunk(w.B, lt, 4 * (1 - t) + j, got);
-                }
-            }
-            tc::fence_proxy_async();
-            tc::fence_before_sync();
-            wg_sync(g);
-            if (lt == 0) {
-                tc::fence_after_sync();
-                mma_k64<64>(tb, w.B, s.t.W2);
-                tc::mma_commit(&w.mbar);
-            }
-            if (!wg_wait(w, phase, g)) { alive = false; break; }
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {   // value rows: silu(z2); tangent rows: silu'(z2) dz2
-                float z[16];
-                tc::tmem_ld16(tl + 16 * h, z);
-                tc::tmem_wait_ld();
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float zv = __shfl_sync(0xffffffffu, z[q], lane & ~1);
-                    const float sg = sigmoid_fast(zv);
-                    z[q] = (lane & 1) ? sg * fmaf(zv, 1.f - sg, 1.f) * z[q] : zv * sg;
-                }
-                st_row_chunk(w.B, lt, 2 * h, z);
-                st_row_chunk(w.B, lt, 2 * h + 1, z + 8);
-            }
-            tc::fence_proxy_async();
-            tc::fence_before_sync();
-            wg_sync(g);
-            if (lt == 0) {
-                tc::fence_after_sync();
-#pragma unroll
-                for (int q = 0; q < PP::NP; ++q) mma_k64<16>(tb + 16 * q, s.t.W3[q], w.B);
-                tc::mma_commit(&w.mbar);
-            }
-            for (int sl = 0; sl < SCB / 8; ++sl) {
-                if (!wg_wait(w, phase, g)) { alive = false; break; }
-                float ajc[TNLM], hjc[TNLM], ajn[TNLM], hjn[TNLM];
-                {
-                    const int64_t jb = ((int64_t)w.col[sl * 8] * TNLM) * TF + c;
-#pragma unroll
-                    for (int q = 0; q < TNLM; ++q) {
-                        ajc[q] = __ldg(Alpha + jb + q * TF);
-                        hjc[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + jb + q * TF);
+                        for (int q = 0; q < 8; ++q) got[q] = __shfl_xor_sync(0xffffffffu, give[q], 1);
+                        st_row_chunk(w.B, lt, 4 * t + j, keep);
+                        st_row_chunk(w.B, lt, 4 * (1 - t) + j, got);
                     }
                 }
-                // one edge of the slice: gathers of edge i in (ajc, hjc); those of
-                // edge i + 1 are fetched into (ajn, hjn) meanwhile; the caller
-                // swaps the roles of the two buffers, so nothing is copied
-                auto edge_step = [&](int i, float (&ajc)[TNLM], float (&hjc)[TNLM],
-                                     float (&ajn)[TNLM], float (&hjn)[TNLM]) -> bool {
-                    const int e = sl * 8 + i;
-                    const int lr = w.row[e];
-                    if (lr < 0) return false;
-                    float R[PP::NP], dR[PP::NP];
-#pragma unroll
-                    for (int q = 0; q < PP::NP; ++q) {
-                        float v2[2];
-                        tc::tmem_ld2(tl + 16 * q + 2 * i, v2);
-                        R[q] = v2[0];
-                        dR[q] = v2[1];
-                    }
-                    if (i + 1 < 8) {
-                        const int64_t jn = ((int64_t)w.col[e + 1] * TNLM) * TF + c;
-#pragma unroll
-                        for (int q = 0; q < TNLM; ++q) {
-                            ajn[q] = __ldg(Alpha + jn + q * TF);
-                            hjn[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + jn + q * TF);
-                        }
-                    }
-                    if (lr != cur) {
-                        if (cur >= 0) {
-                            fold();
-                            flush(cur, true);
-                            next = cur + 1;
-                        }
-                        for (int q = next; q < lr; ++q) flush(q, false);
-                        next = lr;
-                        cur = lr;
-                        const int64_t base = ((r0 + lr) * TNLM) * TF + c;
-#pragma unroll
-                        for (int q = 0; q < TNLM; ++q) {
-                            gacc[q] = 0.f;
-                            ak[q] = __ldg(Alpha + base + q * TF);
-                            hk[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + base + q * TF);
-                        }
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) fk[q] = fc[q] = 0.f;
-                        if (STRESS) {
-#pragma unroll
-                            for (int q = 0; q < 9; ++q) va[q] = 0.f;
-                        }
-                    }
-                    tc::tmem_wait_ld();
-                    float Y[TNLM];
-                    {
-                        const float4 y0 = *reinterpret_cast<const float4*>(&w.Y[e][0]);
-                        const float4 y1 = *reinterpret_cast<const float4*>(&w.Y[e][4]);
-                        Y[0] = 1.f;
-                        Y[1] = y0.x; Y[2] = y0.y; Y[3] = y0.z; Y[4] = y0.w;
-                        Y[5] = y1.x; Y[6] = y1.y; Y[7] = y1.z; Y[8] = y1.w;
-                    }
-                    const float hj0 = hjc[0], hk0 = hk[0];
-                    float gr, gy[TNLM];
-                    gy[0] = 0.f;
-                    if (FIRST) {
-                        // layer 0 (no l >= 1 inputs): P_lm = hj0 ak_lm -+ hk0 aj_lm enters
-                        // both the radial term (through P_l . Y_l) and dE/dY (R_la P_lm)
-                        float s1 = 0.f, s2 = 0.f;
-#pragma unroll
-                        for (int m = 0; m < 3; ++m) {
-                            const float P = fmaf(hj0, ak[1 + m], -hk0 * ajc[1 + m]);
-                            s1 = fmaf(P, Y[1 + m], s1);
-                            gy[1 + m] = R[PP::sla(1)] * P;
-                        }
-#pragma unroll
-                        for (int m = 0; m < 5; ++m) {
-                            const float P = fmaf(hj0, ak[4 + m], hk0 * ajc[4 + m]);
-                            s2 = fmaf(P, Y[4 + m], s2);
-                            gy[4 + m] = R[PP::sla(2)] * P;
-                        }
-                        gr = fmaf(ak[0], hj0, ajc[0] * hk0) * dR[0];
-                        gr = fmaf(s1, dR[PP::sla(1)], gr);
-                        gr = fmaf(s2, dR[PP::sla(2)], gr);
-                    } else {
-                    // Y-weighted sums of the sender's (j) and receiver's (k) alpha
-                    float sj1 = 0.f, sk1 = 0.f, sj2 = 0.f, sk2 = 0.f;
-#pragma unroll
-                    for (int m = 0; m < 3; ++m) {
-                        sj1 = fmaf(ajc[1 + m], Y[1 + m], sj1);
-                        sk1 = fmaf(ak[1 + m], Y[1 + m], sk1);
-                    }
-#pragma unroll
-                    for (int m = 0; m < 5; ++m) {
-                        sj2 = fmaf(ajc[4 + m], Y[4 + m], sj2);
-                        sk2 = fmaf(ak[4 + m], Y[4 + m], sk2);
-                    }
-                    {   // dE/dh_k as the sender of the reverse edge (i <- k)
-                        float g0 = R[0] * ajc[0];
-                        g0 = fmaf(-R[PP::sla(1)], sj1, g0);
-                        g0 = fmaf(R[PP::sla(2)], sj2, g0);
-                        gacc[0] += g0;
-#pragma unroll
-                        for (int m = 0; m < 3; ++m) gacc[1 + m] = fmaf(R[PP::slb(1)], ajc[1 + m], gacc[1 + m]);
-#pragma unroll
-                        for (int m = 0; m < 5; ++m) gacc[4 + m] = fmaf(R[PP::slb(2)], ajc[4 + m], gacc[4 + m]);
-                    }
-                    // this channel's share of dE_pair/dd: radial part along u (both
-                    // directions' dE/dR contracted with dR/dr) and the angular part
-                    // through dE/dY; the l = 1 term of the reverse edge changes sign
-                    gr = fmaf(ak[0], hj0, ajc[0] * hk0) * dR[0];
-                    gr = fmaf(fmaf(hj0, sk1, -hk0 * sj1), dR[PP::sla(1)], gr);
-                    gr = fmaf(fmaf(hj0, sk2, hk0 * sj2), dR[PP::sla(2)], gr);
-                    {
-                        float g1b = 0.f, g2b = 0.f;
-#pragma unroll
-                        for (int m = 0; m < 3; ++m)
-                            g1b = fmaf(ak[1 + m], hjc[1 + m], fmaf(ajc[1 + m], hk[1 + m], g1b));
-#pragma unroll
-                        for (int m = 0; m < 5; ++m)
-                            g2b = fmaf(ak[4 + m], hjc[4 + m], fmaf(ajc[4 + m], hk[4 + m], g2b));
-                        gr = fmaf(g1b, dR[PP::slb(1)], gr);
-                        gr = fmaf(g2b, dR[PP::slb(2)], gr);
-                    }
-                    {
-                        const float a1 = R[PP::sla(1)] * hj0, b1 = R[PP::sla(1)] * hk0;
-                        const float a2 = R[PP::sla(2)] * hj0, b2 = R[PP::sla(2)] * hk0;
-#pragma unroll
-                        for (int m = 0; m < 3; ++m) gy[1 + m] = fmaf(ak[1 + m], a1, -ajc[1 + m] * b1);
-#pragma unroll
-                        for (int m = 0; m < 5; ++m) gy[4 + m] = fmaf(ak[4 + m], a2, ajc[4 + m] * b2);
-                    }
-                    }
-                    const float4 ue = *reinterpret_cast<const float4*>(&w.u[e][0]);
-                    const float u[3] = {ue.x, ue.y, ue.z};
-                    const float ir = ue.w;
-                    float v[3];
-                    sph_grad<TLMAX, float>(u, gy, v);
-                    const float vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
-                    if (STRESS) {
-                        // the force share is accumulated exactly as without the
-                        // stress (same operations), gq only feeds the virial
-                        const float t = fmaf(-ir, vu, gr);
-                        float gq[3];
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            fs[q] = fmaf(t, u[q], fmaf(ir, v[q], fs[q]));
-                            gq[q] = fmaf(t, u[q], ir * v[q]);
-                        }
-                        const float r = 1.f / ir;
-#pragma unroll
-                        for (int p = 0; p < 3; ++p)
-#pragma unroll
-                            for (int q = 0; q < 3; ++q) va[3 * p + q] = fmaf(gq[p], u[q] * r, va[3 * p + q]);
-                    } else {   // gr u + (v - (v . u) u) / r, regrouped
-                        const float t = fmaf(-ir, vu, gr);
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) fs[q] = fmaf(t, u[q], fmaf(ir, v[q], fs[q]));
-                    }
-                    return true;
-                };
-#pragma unroll 1
-                for (int i = 0; i < 8; i += 2) {
-                    if (!edge_step(i, ajc, hjc, ajn, hjn)) break;
-                    if (!edge_step(i + 1, ajn, hjn, ajc, hjc)) break;
-                }
-                fold();
+                tc::fence_proxy_async();
                 tc::fence_before_sync();
                 wg_sync(g);
-                if (lt == 0 && sl + 1 < SCB / 8) {
+                if (lt == 0) {
                     tc::fence_after_sync();
-#pragma unroll
-                    for (int q = 0; q < PP::NP; ++q)
-                        mma_k64<16>(tb + 16 * q, s.t.W3[q], w.B + (sl + 1) * 16 * 64);
+                    mma_k64<64>(tb, w.B, s.t.W2);
                     tc::mma_commit(&w.mbar);
                 }
+                if (!wg_wait(w, phase, g)) { alive = false; break; }
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {   // value rows: silu(z2); tangent rows: silu'(z2) dz2
+                    float z[16];
+                    tc::tmem_ld16(tl + 16 * h, z);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float zv = __shfl_sync(0xffffffffu, z[q], lane & ~1);
+                        const float sg = sigmoid_fast(zv);
+                        z[q] = (lane & 1) ? sg * fmaf(zv, 1.f - sg, 1.f) * z[q] : zv * sg;
+                    }
+                    st_row_chunk(w.B, lt, 2 * h, z);
+                    st_row_chunk(w.B, lt, 2 * h + 1, z + 8);
+                }
+                tc::fence_proxy_async();
+                tc::fence_before_sync();
+                wg_sync(g);
+                if (lt == 0) {
+                    tc::fence_after_sync();
+#pragma unroll
+                    for (int q = 0; q < PP::NP; ++q) mma_k64<16>(tb + 16 * q, s.t.W3[q], w.B);
+                    tc::mma_commit(&w.mbar);
+                }
+                for (int sl = 0; sl < SCB / 8; ++sl) {
+                    if (!wg_wait(w, phase, g)) { alive = false; break; }
+                    float ajc[TNLM], hjc[TNLM], ajn[TNLM], hjn[TNLM];
+                    {
+                        const int64_t jb = ((int64_t)w.col[sl * 8] * TNLM) * TF + c;
+#pragma unroll
+                        for (int q = 0; q < TNLM; ++q) {
+                            ajc[q] = __ldg(Alpha + jb + q * TF);
+                            hjc[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + jb + q * TF);
+                        }
+                    }
+                    // one edge of the slice: gathers of edge i in (ajc, hjc); those of
+                    // edge i + 1 are fetched into (ajn, hjn) meanwhile; the caller
+                    // swaps the roles of the two buffers, so nothing is copied
+                    auto edge_step = [&](int i, float (&ajc)[TNLM], float (&hjc)[TNLM],
+                                         float (&ajn)[TNLM], float (&hjn)[TNLM]) -> bool {
+                        const int e = sl * 8 + i;
+                        const int lr = w.row[e];
+                        if (lr < 0) return false;
+                        float R[PP::NP], dR[PP::NP];
+#pragma unroll
+                        for (int q = 0; q < PP::NP; ++q) {
+                            float v2[2];
+                            tc::tmem_ld2(tl + 16 * q + 2 * i, v2);
+                            R[q] = v2[0];
+                            dR[q] = v2[1];
+                        }
+                        if (i + 1 < 8) {
+                            const int64_t jn = ((int64_t)w.col[e + 1] * TNLM) * TF + c;
+#pragma unroll
+                            for (int q = 0; q < TNLM; ++q) {
+                                ajn[q] = __ldg(Alpha + jn + q * TF);
+                                hjn[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + jn + q * TF);
+                            }
+                        }
+                        if (lr != cur) {
+                            if (cur >= 0) {
+                                fold();
+                                flush(cur, true);
+                                next = cur + 1;
+                            }
+                            for (int q = next; q < lr; ++q) flush(q, false);
+                            next = lr;
+                            cur = lr;
+                            const int64_t base = ((r0 + lr) * TNLM) * TF + c;
+#pragma unroll
+                            for (int q = 0; q < TNLM; ++q) {
+                                gacc[q] = 0.f;
+                                ak[q] = __ldg(Alpha + base + q * TF);
+                                hk[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + base + q * TF);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) fk[q] = fc[q] = 0.f;
+                            if (STRESS) {
+#pragma unroll
+                                for (int q = 0; q < 9; ++q) va[q] = 0.f;
+                            }
+                        }
+                        tc::tmem_wait_ld();
+                        float Y[TNLM];
+                        {
+                            const float4 y0 = *reinterpret_cast<const float4*>(&w.Y[e][0]);
+                            const float4 y1 = *reinterpret_cast<const float4*>(&w.Y[e][4]);
+                            Y[0] = 1.f;
+                            Y[1] = y0.x; Y[2] = y0.y; Y[3] = y0.z; Y[4] = y0.w;
+                            Y[5] = y1.x; Y[6] = y1.y; Y[7] = y1.z; Y[8] = y1.w;
+                        }
+                        const float hj0 = hjc[0], hk0 = hk[0];
+                        float gr, gy[TNLM];
+                        gy[0] = 0.f;
+                        if (FIRST) {
+                            // layer 0 (no l >= 1 inputs): P_lm = hj0 ak_lm -+ hk0 aj_lm enters
+                            // both the radial term (through P_l . Y_l) and dE/dY (R_la P_lm)
+                            float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+                            for (int m = 0; m < 3; ++m) {
+                                const float P = fmaf(hj0, ak[1 + m], -hk0 * ajc[1 + m]);
+                                s1 = fmaf(P, Y[1 + m], s1);
+                                gy[1 + m] = R[PP::sla(1)] * P;
+                            }
+#pragma unroll
+                            for (int m = 0; m < 5; ++m) {
+                                const float P = fmaf(hj0, ak[4 + m], hk0 * ajc[4 + m]);
+                                s2 = fmaf(P, Y[4 + m], s2);
+                                gy[4 + m] = R[PP::sla(2)] * P;
+                            }
+                            gr = fmaf(ak[0], hj0, ajc[0] * hk0) * dR[0];
+                            gr = fmaf(s1, dR[PP::sla(1)], gr);
+                            gr = fmaf(s2, dR[PP::sla(2)], gr);
+                        } else {
+                            // Y-weighted sums of the sender's (j) and receiver's (k) alpha
+                            float sj1 = 0.f, sk1 = 0.f, sj2 = 0.f, sk2 = 0.f;
+#pragma unroll
+                            for (int m = 0; m < 3; ++m) {
+                                sj1 = fmaf(ajc[1 + m], Y[1 + m], sj1);
+                                sk1 = fmaf(ak[1 + m], Y[1 + m], sk1);
+                            }
+#pragma unroll
+                            for (int m = 0; m < 5; ++m) {
+                                sj2 = fmaf(ajc[4 + m], Y[4 + m], sj2);
+                                sk2 = fmaf(ak[4 + m], Y[4 + m], sk2);
+                            }
+                            {   // dE/dh_k as the sender of the reverse edge (i <- k)
+                                float g0 = R[0] * ajc[0];
+                                g0 = fmaf(-R[PP::sla(1)], sj1, g0);
+                                g0 = fmaf(R[PP::sla(2)], sj2, g0);
+                                gacc[0] += g0;
+#pragma unroll
+                                for (int m = 0; m < 3; ++m) gacc[1 + m] = fmaf(R[PP::slb(1)], ajc[1 + m], gacc[1 + m]);
+#pragma unroll
+                                for (int m = 0; m < 5; ++m) gacc[4 + m] = fmaf(R[PP::slb(2)], ajc[4 + m], gacc[4 + m]);
+                            }
+                            // this channel's share of dE_pair/dd: radial part along u (both
+                            // directions' dE/dR contracted with dR/dr) and the angular part
+                            // through dE/dY; the l = 1 term of the reverse edge changes sign
+                            gr = fmaf(ak[0], hj0, ajc[0] * hk0) * dR[0];
+                            gr = fmaf(fmaf(hj0, sk1, -hk0 * sj1), dR[PP::sla(1)], gr);
+                            gr = fmaf(fmaf(hj0, sk2, hk0 * sj2), dR[PP::sla(2)], gr);
+                            {
+                                float g1b = 0.f, g2b = 0.f;
+#pragma unroll
+                                for (int m = 0; m < 3; ++m)
+                                    g1b = fmaf(ak[1 + m], hjc[1 + m], fmaf(ajc[1 + m], hk[1 + m], g1b));
+#pragma unroll
+                                for (int m = 0; m < 5; ++m)
+                                    g2b = fmaf(ak[4 + m], hjc[4 + m], fmaf(ajc[4 + m], hk[4 + m], g2b));
+                                gr = fmaf(g1b, dR[PP::slb(1)], gr);
+                                gr = fmaf(g2b, dR[PP::slb(2)], gr);
+                            }
+                            {
+                                const float a1 = R[PP::sla(1)] * hj0, b1 = R[PP::sla(1)] * hk0;
+                                const float a2 = R[PP::sla(2)] * hj0, b2 = R[PP::sla(2)] * hk0;
+#pragma unroll
+                                for (int m = 0; m < 3; ++m) gy[1 + m] = fmaf(ak[1 + m], a1, -ajc[1 + m] * b1);
+#pragma unroll
+                                for (int m = 0; m < 5; ++m) gy[4 + m] = fmaf(ak[4 + m], a2, ajc[4 + m] * b2);
+                            }
+                        }
+                        const float4 ue = *reinterpret_cast<const float4*>(&w.u[e][0]);
+                        const float u[3] = {ue.x, ue.y, ue.z};
+                        const float ir = ue.w;
+                        float v[3];
+                        sph_grad<TLMAX, float>(u, gy, v);
+                        const float vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
+                        if (STRESS) {
+                            // the force share is accumulated exactly as without the
+                            // stress (same operations), gq only feeds the virial
+                            const float t = fmaf(-ir, vu, gr);
+                            float gq[3];
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) {
+                                fs[q] = fmaf(t, u[q], fmaf(ir, v[q], fs[q]));
+                                gq[q] = fmaf(t, u[q], ir * v[q]);
+                            }
+                            const float r = 1.f / ir;
+#pragma unroll
+                            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                                for (int q = 0; q < 3; ++q) va[3 * p + q] = fmaf(gq[p], u[q] * r, va[3 * p + q]);
+                        } else {   // gr u + (v - (v . u) u) / r, regrouped
+                            const float t = fmaf(-ir, vu, gr);
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) fs[q] = fmaf(t, u[q], fmaf(ir, v[q], fs[q]));
+                        }
+                        return true;
+                    };
+#pragma unroll 1
+                    for (int i = 0; i < 8; i += 2) {
+                        if (!edge_step(i, ajc, hjc, ajn, hjn)) break;
+                        if (!edge_step(i + 1, ajn, hjn, ajc, hjc)) break;
+                    }
+                    fold();
+                    tc::fence_before_sync();
+                    wg_sync(g);
+                    if (lt == 0 && sl + 1 < SCB / 8) {
+                        tc::fence_after_sync();
+#pragma unroll
+                        for (int q = 0; q < PP::NP; ++q)
+                            mma_k64<16>(tb + 16 * q, s.t.W3[q], w.B + (sl + 1) * 16 * 64);
+                        tc::mma_commit(&w.mbar);
+                    }
+                }
             }
-          }
-          wb = we;
+            wb = we;
         }
         if (!alive) break;
         if (cur >= 0) {

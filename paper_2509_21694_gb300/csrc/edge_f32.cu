@@ -321,233 +321,233 @@ __global__ void __launch_bounds__(F) k_edge_bwd(EdgeArgs a, const float* __restr
     const bool compact = a.n_recv > 0 && r0 + nrows > a.n_recv;
     const int lane = c & 31, wid = c >> 5;
     for (int64_t wb = e_beg; wb < e_end;) {
-      const int64_t we = compact ? min(wb + (int64_t)(4 * F), e_end) : e_end;
-      int64_t nk = we - wb;
-      if (compact) {
-          int keep[4], cnt = 0;
+        const int64_t we = compact ? min(wb + (int64_t)(4 * F), e_end) : e_end;
+        int64_t nk = we - wb;
+        if (compact) {
+            int keep[4], cnt = 0;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-              const int64_t e = wb + 4 * c + q;
-              keep[q] = 0;
-              if (e < we) {
-                  const int lr = find_row(s.rp, nrows, e);
-                  keep[q] = !(r0 + lr >= a.n_recv && (int64_t)a.col[e] >= a.n_recv);
-              }
-              cnt += keep[q];
-          }
-          int inc = cnt;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-              const int y = __shfl_up_sync(0xffffffffu, inc, o);
-              if (lane >= o) inc += y;
-          }
-          if (lane == 31) s.kwarp[wid] = inc;
-          __syncthreads();
-          int off = inc - cnt;
-          for (int q = 0; q < wid; ++q) off += s.kwarp[q];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-              if (keep[q]) s.klist[off++] = 4 * c + q;
-          nk = 0;
-          for (int q = 0; q < F / 32; ++q) nk += s.kwarp[q];
-          __syncthreads();
-      }
-      for (int64_t cb = 0; cb < nk; cb += CB) {
-        if (c < CB) {
-            const int64_t v = cb + c;
-            const int64_t e = v < nk ? wb + (compact ? (int64_t)s.klist[v] : v) : e_end;
-            float eps[kNB], deps[kNB], Y[NLM], u4[4] = {0.f, 0.f, 0.f, 1.f};
-            if (e < e_end) {
-                const int lr = find_row(s.rp, nrows, e);
-                const int j = a.col[e];
-                float d[3];
-                edge_vector(a.x, r0 + lr, j, a.shift[e], a.k, d);
-                const float r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-                u4[0] = d[0] / r;
-                u4[1] = d[1] / r;
-                u4[2] = d[2] / r;
-                u4[3] = r;
-                float env, denv;
-                radial_basis<true>(r, a.k, eps, deps, env, denv);
-                sph_harm<LMAX>(u4, Y);
-                s.row[c] = lr;
-                s.col[c] = j;
-            } else {
-#pragma unroll
-                for (int q = 0; q < kNB; ++q) eps[q] = deps[q] = 0.f;
-#pragma unroll
-                for (int q = 0; q < NLM; ++q) Y[q] = 0.f;
-                s.row[c] = -1;
-                s.col[c] = 0;
+            for (int q = 0; q < 4; ++q) {
+                const int64_t e = wb + 4 * c + q;
+                keep[q] = 0;
+                if (e < we) {
+                    const int lr = find_row(s.rp, nrows, e);
+                    keep[q] = !(r0 + lr >= a.n_recv && (int64_t)a.col[e] >= a.n_recv);
+                }
+                cnt += keep[q];
             }
+            int inc = cnt;
 #pragma unroll
-            for (int q = 0; q < kNB; ++q) {
-                s.eps[c][q] = eps[q];
-                s.deps[c][q] = deps[q];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
             }
+            if (lane == 31) s.kwarp[wid] = inc;
+            __syncthreads();
+            int off = inc - cnt;
+            for (int q = 0; q < wid; ++q) off += s.kwarp[q];
 #pragma unroll
-            for (int q = 0; q < NLM; ++q) s.Y[c][q] = Y[q];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) s.u[c][q] = u4[q];
+            for (int q = 0; q < 4; ++q)
+                if (keep[q]) s.klist[off++] = 4 * c + q;
+            nk = 0;
+            for (int q = 0; q < F / 32; ++q) nk += s.kwarp[q];
+            __syncthreads();
         }
-        __syncthreads();
-        for (int o = c; o < kH * CB; o += F) {
-            const int kk = o / CB, e = o % CB;
-            float z = 0.f, dz = 0.f;
+        for (int64_t cb = 0; cb < nk; cb += CB) {
+            if (c < CB) {
+                const int64_t v = cb + c;
+                const int64_t e = v < nk ? wb + (compact ? (int64_t)s.klist[v] : v) : e_end;
+                float eps[kNB], deps[kNB], Y[NLM], u4[4] = {0.f, 0.f, 0.f, 1.f};
+                if (e < e_end) {
+                    const int lr = find_row(s.rp, nrows, e);
+                    const int j = a.col[e];
+                    float d[3];
+                    edge_vector(a.x, r0 + lr, j, a.shift[e], a.k, d);
+                    const float r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                    u4[0] = d[0] / r;
+                    u4[1] = d[1] / r;
+                    u4[2] = d[2] / r;
+                    u4[3] = r;
+                    float env, denv;
+                    radial_basis<true>(r, a.k, eps, deps, env, denv);
+                    sph_harm<LMAX>(u4, Y);
+                    s.row[c] = lr;
+                    s.col[c] = j;
+                } else {
 #pragma unroll
-            for (int b = 0; b < kNB; ++b) {
-                const float wv = __ldg(&W1[kk * kNB + b]);
-                z = fmaf(wv, s.eps[e][b], z);
-                dz = fmaf(wv, s.deps[e][b], dz);
+                    for (int q = 0; q < kNB; ++q) eps[q] = deps[q] = 0.f;
+#pragma unroll
+                    for (int q = 0; q < NLM; ++q) Y[q] = 0.f;
+                    s.row[c] = -1;
+                    s.col[c] = 0;
+                }
+#pragma unroll
+                for (int q = 0; q < kNB; ++q) {
+                    s.eps[c][q] = eps[q];
+                    s.deps[c][q] = deps[q];
+                }
+#pragma unroll
+                for (int q = 0; q < NLM; ++q) s.Y[c][q] = Y[q];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) s.u[c][q] = u4[q];
             }
-            s.a1[kk][e] = silu(z);
-            s.da1[kk][e] = silu_grad(z) * dz;
-        }
-        __syncthreads();
-        {
-            const int kk = c % kH, e0 = (c / kH) * EG;
-            float z[EG], dz[EG];
+            __syncthreads();
+            for (int o = c; o < kH * CB; o += F) {
+                const int kk = o / CB, e = o % CB;
+                float z = 0.f, dz = 0.f;
 #pragma unroll
-            for (int q = 0; q < EG; ++q) z[q] = dz[q] = 0.f;
+                for (int b = 0; b < kNB; ++b) {
+                    const float wv = __ldg(&W1[kk * kNB + b]);
+                    z = fmaf(wv, s.eps[e][b], z);
+                    dz = fmaf(wv, s.deps[e][b], dz);
+                }
+                s.a1[kk][e] = silu(z);
+                s.da1[kk][e] = silu_grad(z) * dz;
+            }
+            __syncthreads();
+            {
+                const int kk = c % kH, e0 = (c / kH) * EG;
+                float z[EG], dz[EG];
+#pragma unroll
+                for (int q = 0; q < EG; ++q) z[q] = dz[q] = 0.f;
 #pragma unroll 4
-            for (int jj = 0; jj < kH; ++jj) {
-                const float wv = __ldg(&W2T[jj * kH + kk]);
+                for (int jj = 0; jj < kH; ++jj) {
+                    const float wv = __ldg(&W2T[jj * kH + kk]);
+#pragma unroll
+                    for (int q = 0; q < EG; ++q) {
+                        z[q] = fmaf(wv, s.a1[jj][e0 + q], z[q]);
+                        dz[q] = fmaf(wv, s.da1[jj][e0 + q], dz[q]);
+                    }
+                }
 #pragma unroll
                 for (int q = 0; q < EG; ++q) {
-                    z[q] = fmaf(wv, s.a1[jj][e0 + q], z[q]);
-                    dz[q] = fmaf(wv, s.da1[jj][e0 + q], dz[q]);
+                    s.a2[kk][e0 + q] = silu(z[q]);
+                    s.da2[kk][e0 + q] = silu_grad(z[q]) * dz[q];
                 }
             }
-#pragma unroll
-            for (int q = 0; q < EG; ++q) {
-                s.a2[kk][e0 + q] = silu(z[q]);
-                s.da2[kk][e0 + q] = silu_grad(z[q]) * dz[q];
-            }
-        }
-        __syncthreads();
-        float R[PP::NP][CB], dR[PP::NP][CB];
-        radial_out2<F, LMAX, FIRST>(W3T, s.a2, s.da2, c, R, dR);
+            __syncthreads();
+            float R[PP::NP][CB], dR[PP::NP][CB];
+            radial_out2<F, LMAX, FIRST>(W3T, s.a2, s.da2, c, R, dR);
 
 #pragma unroll
-        for (int e = 0; e < CB; ++e) {
-            const int lr = s.row[e];
-            if (lr < 0) {
+            for (int e = 0; e < CB; ++e) {
+                const int lr = s.row[e];
+                if (lr < 0) {
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) s.part[e][q][c] = 0.f;
-                continue;
-            }
-            if (lr != cur) {
-                if (cur >= 0) {
-                    flush(cur, true);
-                    next = cur + 1;
+                    for (int q = 0; q < NQ; ++q) s.part[e][q][c] = 0.f;
+                    continue;
                 }
-                for (int q = next; q < lr; ++q) flush(q, false);
-                next = lr;
-                cur = lr;
-                const int64_t base = ((r0 + lr) * NLM) * F + c;
+                if (lr != cur) {
+                    if (cur >= 0) {
+                        flush(cur, true);
+                        next = cur + 1;
+                    }
+                    for (int q = next; q < lr; ++q) flush(q, false);
+                    next = lr;
+                    cur = lr;
+                    const int64_t base = ((r0 + lr) * NLM) * F + c;
+#pragma unroll
+                    for (int q = 0; q < NLM; ++q) {
+                        gacc[q] = 0.f;
+                        ak[q] = a.Alpha[base + q * F];
+                        hk[q] = (FIRST && q > 0) ? 0.f : a.Hin[base + q * F];
+                    }
+                }
+                const int64_t jb = ((int64_t)s.col[e] * NLM) * F + c;
+                float aj[NLM], hj[NLM];
 #pragma unroll
                 for (int q = 0; q < NLM; ++q) {
-                    gacc[q] = 0.f;
-                    ak[q] = a.Alpha[base + q * F];
-                    hk[q] = (FIRST && q > 0) ? 0.f : a.Hin[base + q * F];
+                    aj[q] = a.Alpha[jb + q * F];
+                    hj[q] = (FIRST && q > 0) ? 0.f : a.Hin[jb + q * F];
                 }
-            }
-            const int64_t jb = ((int64_t)s.col[e] * NLM) * F + c;
-            float aj[NLM], hj[NLM];
+                float Y[NLM];
 #pragma unroll
-            for (int q = 0; q < NLM; ++q) {
-                aj[q] = a.Alpha[jb + q * F];
-                hj[q] = (FIRST && q > 0) ? 0.f : a.Hin[jb + q * F];
-            }
-            float Y[NLM];
+                for (int q = 0; q < NLM; ++q) Y[q] = s.Y[e][q];
+                // (a) dE/dh_k as the sender of the reverse edge (i <- k)
+                if (!FIRST) {
+                    float g0 = R[0][e] * aj[0];
+                    float sm1 = 0.f;
 #pragma unroll
-            for (int q = 0; q < NLM; ++q) Y[q] = s.Y[e][q];
-            // (a) dE/dh_k as the sender of the reverse edge (i <- k)
-            if (!FIRST) {
-                float g0 = R[0][e] * aj[0];
-                float sm1 = 0.f;
+                    for (int m = 0; m < 3; ++m) {
+                        sm1 = fmaf(aj[1 + m], Y[1 + m], sm1);
+                        gacc[1 + m] = fmaf(R[PP::slb(1)][e], aj[1 + m], gacc[1 + m]);
+                    }
+                    g0 = fmaf(-R[PP::sla(1)][e], sm1, g0);
+                    if (LMAX >= 2) {
+                        float sm2 = 0.f;
 #pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    sm1 = fmaf(aj[1 + m], Y[1 + m], sm1);
-                    gacc[1 + m] = fmaf(R[PP::slb(1)][e], aj[1 + m], gacc[1 + m]);
+                        for (int m = 0; m < 5; ++m) {
+                            sm2 = fmaf(aj[4 + m], Y[4 + m], sm2);
+                            gacc[4 + m] = fmaf(R[PP::slb(2)][e], aj[4 + m], gacc[4 + m]);
+                        }
+                        g0 = fmaf(R[PP::sla(2)][e], sm2, g0);
+                    }
+                    gacc[0] += g0;
                 }
-                g0 = fmaf(-R[PP::sla(1)][e], sm1, g0);
+                // (b) dE/dR of both directions contracted with dR/dr; (c) dE/dY
+                float gr = (ak[0] * hj[0] + aj[0] * hk[0]) * dR[0][e];
+                {
+                    float g1a = 0.f, g1b = 0.f;
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        const float t = ak[1 + m] * hj[0] - aj[1 + m] * hk[0];
+                        g1a = fmaf(Y[1 + m], t, g1a);
+                        s.part[e][1 + m][c] = R[PP::sla(1)][e] * t;
+                        if (!FIRST) g1b += ak[1 + m] * hj[1 + m] + aj[1 + m] * hk[1 + m];
+                    }
+                    gr = fmaf(g1a, dR[PP::sla(1)][e], gr);
+                    if (!FIRST) gr = fmaf(g1b, dR[PP::slb(1)][e], gr);
+                }
                 if (LMAX >= 2) {
-                    float sm2 = 0.f;
+                    float g2a = 0.f, g2b = 0.f;
 #pragma unroll
                     for (int m = 0; m < 5; ++m) {
-                        sm2 = fmaf(aj[4 + m], Y[4 + m], sm2);
-                        gacc[4 + m] = fmaf(R[PP::slb(2)][e], aj[4 + m], gacc[4 + m]);
+                        const float t = ak[4 + m] * hj[0] + aj[4 + m] * hk[0];
+                        g2a = fmaf(Y[4 + m], t, g2a);
+                        s.part[e][4 + m][c] = R[PP::sla(2)][e] * t;
+                        if (!FIRST) g2b += ak[4 + m] * hj[4 + m] + aj[4 + m] * hk[4 + m];
                     }
-                    g0 = fmaf(R[PP::sla(2)][e], sm2, g0);
+                    gr = fmaf(g2a, dR[PP::sla(2)][e], gr);
+                    if (!FIRST) gr = fmaf(g2b, dR[PP::slb(2)][e], gr);
                 }
-                gacc[0] += g0;
+                s.part[e][0][c] = gr;
             }
-            // (b) dE/dR of both directions contracted with dR/dr; (c) dE/dY
-            float gr = (ak[0] * hj[0] + aj[0] * hk[0]) * dR[0][e];
-            {
-                float g1a = 0.f, g1b = 0.f;
+            __syncthreads();
+            for (int t = c; t < CB * NQ; t += F) s.red[t / NQ][t % NQ] = kahan_sum(s.part[t / NQ][t % NQ], F);
+            __syncthreads();
+            if (c < CB && s.row[c] >= 0) {
+                const int e = c;
+                const double gr = s.red[e][0];
+                double gY[NLM];
+                gY[0] = 0.0;
 #pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    const float t = ak[1 + m] * hj[0] - aj[1 + m] * hk[0];
-                    g1a = fmaf(Y[1 + m], t, g1a);
-                    s.part[e][1 + m][c] = R[PP::sla(1)][e] * t;
-                    if (!FIRST) g1b += ak[1 + m] * hj[1 + m] + aj[1 + m] * hk[1 + m];
+                for (int q = 1; q < NLM; ++q) gY[q] = s.red[e][q];
+                const double u[3] = {s.u[e][0], s.u[e][1], s.u[e][2]};
+                const double ir = 1.0 / (double)s.u[e][3];
+                double v[3];
+                sph_grad<LMAX, double>(u, gY, v);
+                const double vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) s.red[e][q] = gr * u[q] + (v[q] - vu * u[q]) * ir;
+            }
+            __syncthreads();
+            // one thread per output component, each summing the chunk's edges in order
+            if (c < 3) {
+                for (int e = 0; e < CB; ++e) {
+                    const int lr = s.row[e];
+                    if (lr < 0) break;
+                    s.frow[lr][c] += s.red[e][c];
                 }
-                gr = fmaf(g1a, dR[PP::sla(1)][e], gr);
-                if (!FIRST) gr = fmaf(g1b, dR[PP::slb(1)][e], gr);
-            }
-            if (LMAX >= 2) {
-                float g2a = 0.f, g2b = 0.f;
-#pragma unroll
-                for (int m = 0; m < 5; ++m) {
-                    const float t = ak[4 + m] * hj[0] + aj[4 + m] * hk[0];
-                    g2a = fmaf(Y[4 + m], t, g2a);
-                    s.part[e][4 + m][c] = R[PP::sla(2)][e] * t;
-                    if (!FIRST) g2b += ak[4 + m] * hj[4 + m] + aj[4 + m] * hk[4 + m];
+            } else if (a.vir && c < 12) {
+                const int p = (c - 3) / 3, q = (c - 3) % 3;
+                for (int e = 0; e < CB; ++e) {
+                    const int lr = s.row[e];
+                    if (lr < 0) break;
+                    s.vrow[lr][3 * p + q] += s.red[e][p] * ((double)s.u[e][q] * (double)s.u[e][3]);
                 }
-                gr = fmaf(g2a, dR[PP::sla(2)][e], gr);
-                if (!FIRST) gr = fmaf(g2b, dR[PP::slb(2)][e], gr);
             }
-            s.part[e][0][c] = gr;
+            __syncthreads();
         }
-        __syncthreads();
-        for (int t = c; t < CB * NQ; t += F) s.red[t / NQ][t % NQ] = kahan_sum(s.part[t / NQ][t % NQ], F);
-        __syncthreads();
-        if (c < CB && s.row[c] >= 0) {
-            const int e = c;
-            const double gr = s.red[e][0];
-            double gY[NLM];
-            gY[0] = 0.0;
-#pragma unroll
-            for (int q = 1; q < NLM; ++q) gY[q] = s.red[e][q];
-            const double u[3] = {s.u[e][0], s.u[e][1], s.u[e][2]};
-            const double ir = 1.0 / (double)s.u[e][3];
-            double v[3];
-            sph_grad<LMAX, double>(u, gY, v);
-            const double vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) s.red[e][q] = gr * u[q] + (v[q] - vu * u[q]) * ir;
-        }
-        __syncthreads();
-        // one thread per output component, each summing the chunk's edges in order
-        if (c < 3) {
-            for (int e = 0; e < CB; ++e) {
-                const int lr = s.row[e];
-                if (lr < 0) break;
-                s.frow[lr][c] += s.red[e][c];
-            }
-        } else if (a.vir && c < 12) {
-            const int p = (c - 3) / 3, q = (c - 3) % 3;
-            for (int e = 0; e < CB; ++e) {
-                const int lr = s.row[e];
-                if (lr < 0) break;
-                s.vrow[lr][3 * p + q] += s.red[e][p] * ((double)s.u[e][q] * (double)s.u[e][3]);
-            }
-        }
-        __syncthreads();
-      }
-      wb = we;
+        wb = we;
     }
     if (cur >= 0) {
         flush(cur, true);
