@@ -54,3 +54,14 @@ def test_binding_raises_without_library(lib_path, tmp_path, monkeypatch):
     monkeypatch.setattr(b, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         b._load()
+
+
+def test_header_is_plain_c():
+    """include/mpip.h is a C header (no C++ or torch types in the ABI)."""
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    r = subprocess.run([cc, "-fsyntax-only", "-Wall", "-Werror", "-x", "c",
+                        os.path.join(ROOT, "include", "mpip.h")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
