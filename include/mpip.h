@@ -175,6 +175,20 @@ int mp_partition_assign(mp_ctx* ctx, const mp_graph* g, const int32_t* d_part, i
 int mp_graph_partition(mp_ctx* ctx, const mp_graph* g, int n_parts, double imbalance,
                        uint64_t seed, int32_t* d_part, int64_t* edge_cut_out);
 
+/* The coarsest-level step of mp_graph_partition on its own, on the host:
+ * recursive greedy bisection of a graph given as HOST CSR arrays (each
+ * bisection grows a region from a pseudo-peripheral vertex, adding the
+ * vertex with the largest gain, until it holds its share of the vertex
+ * weight; the best of 8 starts by cut).  No device work; for callers that
+ * hold small host graphs, and for tests of this step.
+ *   row_ptr [n+1] int64 (row_ptr[0] = 0), col [row_ptr[n]] int32 in 0..n-1
+ *   (a symmetric graph), edge_w / vertex_w int32 or NULL (= 1).
+ *   part_out [n] int32, written: 0..n_parts-1.
+ * Errors: MP_ERR_ARG. */
+int mp_partition_host_bisect(int n, const int64_t* row_ptr, const int32_t* col,
+                             const int32_t* edge_w, const int32_t* vertex_w, int n_parts,
+                             uint64_t seed, int32_t* part_out);
+
 /* Host read-back: sizes of partition p. */
 int mp_plan_info(const mp_plan* plan, int p, int64_t* n_ext, int64_t* n_root, int64_t* n_edges);
 /* Extended set of partition p in caller ids and a root flag per entry:

@@ -73,6 +73,7 @@ def _load():
         "mp_partition": (I32, [P, P, I32, I32, I32, PP, ctypes.POINTER(D)]),
         "mp_partition_assign": (I32, [P, P, P, I32, I32, PP, ctypes.POINTER(D)]),
         "mp_graph_partition": (I32, [P, P, I32, D, ctypes.c_uint64, P, ctypes.POINTER(I64)]),
+        "mp_partition_host_bisect": (I32, [I32, P, P, P, P, I32, ctypes.c_uint64, P]),
         "mp_plan_info": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64),
                                ctypes.POINTER(I64)]),
         "mp_plan_export": (I32, [P, I32, P, P]),
@@ -234,6 +235,22 @@ def mp_graph_partition(ctx: int, g: int, n_parts: int, imbalance: float = 0.03, 
     _check(_lib.mp_graph_partition(ctx, g, n_parts, imbalance, seed, _ptr(part),
                                    ctypes.byref(cut)), "mp_graph_partition")
     return part[:n], cut.value
+
+
+def mp_partition_host_bisect(row_ptr, col, n_parts: int, seed: int = 0, edge_w=None,
+                             vertex_w=None) -> np.ndarray:
+    """Recursive greedy bisection of a host CSR graph (numpy arrays); host only."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = len(row_ptr) - 1
+    ew = None if edge_w is None else np.ascontiguousarray(edge_w, dtype=np.int32)
+    vw = None if vertex_w is None else np.ascontiguousarray(vertex_w, dtype=np.int32)
+    part = np.zeros(max(n, 1), dtype=np.int32)
+    _check(_lib.mp_partition_host_bisect(n, row_ptr.ctypes.data, col.ctypes.data if len(col) else None,
+                                         None if ew is None else ew.ctypes.data,
+                                         None if vw is None else vw.ctypes.data, n_parts, seed,
+                                         part.ctypes.data), "mp_partition_host_bisect")
+    return part[:n]
 
 
 def mp_plan_info(plan: int, p: int):

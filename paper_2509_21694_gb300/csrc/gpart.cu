@@ -831,3 +831,32 @@ int graph_partition(mp_ctx* ctx, const Graph& g, int k, double imbalance, uint64
 }
 
 }  // namespace mp
+
+// Host entry to the coarsest-level step alone: recursive greedy bisection
+// of a small graph given as host CSR arrays (no device work).
+extern "C" int mp_partition_host_bisect(int n, const int64_t* row_ptr, const int32_t* col,
+                                        const int32_t* edge_w, const int32_t* vertex_w,
+                                        int n_parts, uint64_t seed, int32_t* part_out) {
+    using namespace mp;
+    if (n < 0 || n_parts < 1 || (n > 0 && (!row_ptr || !part_out)) ||
+        (row_ptr && row_ptr[0] != 0))
+        return MP_ERR_ARG;
+    if (n == 0) return MP_OK;
+    const int64_t m = row_ptr[n];
+    if (m < 0 || (m > 0 && !col)) return MP_ERR_ARG;
+    HostGraph G;
+    G.n = n;
+    G.rp.assign(row_ptr, row_ptr + n + 1);
+    G.col.assign(col, col + m);
+    for (int64_t e = 0; e < m; ++e)
+        if (G.col[e] < 0 || G.col[e] >= n) return MP_ERR_ARG;
+    G.ew = edge_w ? std::vector<int32_t>(edge_w, edge_w + m) : std::vector<int32_t>(m, 1);
+    G.vw = vertex_w ? std::vector<int32_t>(vertex_w, vertex_w + n) : std::vector<int32_t>(n, 1);
+    std::vector<int32_t> verts(n), loc(n, -1), part(n, 0);
+    std::vector<int> seen(n, 0);
+    int stamp = 0;
+    for (int i = 0; i < n; ++i) verts[i] = i;
+    bisect(G, verts, n_parts, 0, seed, 0, loc, seen, stamp, part);
+    std::copy(part.begin(), part.end(), part_out);
+    return MP_OK;
+}
