@@ -28,6 +28,13 @@
 //      (FP32 over a slice, compensated across slices); channels are summed
 //      once per row in FP64,
 //      F_k = sum_e sum_c g_c(e).
+// The adjoint of a layer first compacts each row group's edges, in order,
+// without those between two atoms of the layer's outermost hop class (their
+// terms are exact zeros).  The epilogues gather the next edge's sender
+// features while the current one computes (layer 0 of the forward, which
+// gathers one value per edge, requests a whole slice's at once), and read
+// the radial outputs from tensor memory eight edges at a time (forward) or
+// per edge (adjoint).
 // The MLP's hidden activations use the hardware tanh for the sigmoid: they
 // are rounded to BF16 for the next contraction anyway.
 // One thread issues the MMAs; completion is signalled through an mbarrier
