@@ -123,6 +123,108 @@ def test_dimer_energy_and_force_closed_form(r):
     assert np.allclose(F[0], dEdr * u, atol=1e-8)
 
 
+# ------------------------------------------------ dimer, any depth, l <= 2 --
+
+def _dimer_energy_recursion(r, w, d, n_layers, z=(0, 1)):
+    """Heteronuclear dimer at distance r, any number of layers and lmax <= 2,
+    written without spherical harmonics.
+
+    Atom 0 sees its partner along u, atom 1 along -u.  By induction every
+    l >= 1 feature stays of the form hl_i[c, m] = a_li[c] Y_lm(u_i): it is
+    zero at the start, and a layer adds V_l A_l where A_l[c, m] = beta_li[c]
+    Y_lm(u_i), because the partner's Y_lm(u_j) = (-1)^l Y_lm(u_i).  With
+    sum_m Y_lm^2 = 2l + 1 every quantity is then a channel vector:
+        A0_i   = R0 h0_j / N
+        beta_li = (Rla h0_j + (-1)^l Rlb a_lj) / N,  B_li = (2l + 1) beta_li^2
+        h0_i  += silu(W0 A0_i + sum_l Ul B_li + b),  a_li += Vl beta_li
+    and E = sum_i (w_out . h0_i + e0[z_i])."""
+    x = r / d.r_cut
+    p = d.p_env
+    u = 1 - (p + 1) * (p + 2) / 2 * x ** p + p * (p + 2) * x ** (p + 1) - p * (p + 1) / 2 * x ** (p + 2)
+    k = np.arange(1, d.n_basis + 1)
+    eps = np.sqrt(2 / d.r_cut) * np.sin(k * np.pi * x) / r * u
+    F = d.F
+    h0 = [w["emb"][z[0]].copy(), w["emb"][z[1]].copy()]
+    a = [[np.zeros(F) for _ in range(d.lmax + 1)] for _ in range(2)]
+    for t in range(n_layers):
+        R = w["W3"][t] @ _silu(w["W2"][t] @ _silu(w["W1"][t] @ eps))
+        new_h0, new_a = [], []
+        for i in (0, 1):
+            j = 1 - i
+            s = w["W0"][t] @ (R[:F] * h0[j] / d.n_avg) + w["b"][t]
+            ai = [None]
+            for l in range(1, d.lmax + 1):
+                Rla = R[(2 * l - 1) * F:(2 * l) * F]
+                Rlb = R[(2 * l) * F:(2 * l + 1) * F]
+                beta = (Rla * h0[j] + (-1) ** l * Rlb * a[j][l]) / d.n_avg
+                s = s + w["U%d" % l][t] @ ((2 * l + 1) * beta ** 2)
+                ai.append(a[i][l] + w["V%d" % l][t] @ beta)
+            new_h0.append(h0[i] + _silu(s))
+            new_a.append(ai)
+        h0, a = new_h0, new_a
+    return float(sum(w["w_out"] @ h0[i] + w["e0"][z[i]] for i in (0, 1)))
+
+
+def _dimer_setup(r, n_full=3):
+    d = synth.model_alloy(n_layers_full=n_full)
+    w = synth.make_weights(d, 3, {"e0": 1.0})
+    box = np.array([40.0, 40.0, 40.0])
+    u = _unit(1, 11)[0]
+    pos = np.array([[15.0, 16.0, 17.0], [15.0, 16.0, 17.0] + r * u])
+    return d, w, box, u, pos
+
+
+@pytest.mark.parametrize("r", [1.9, 2.6, 3.7, 5.3])
+def test_dimer_two_and_three_layers_lmax2(r):
+    """Layers >= 2 of the lmax = 2 network: the l >= 1 features made by layer
+    1 (V_l A_l) enter layer 2's messages through R_lb, and B_2 through U_2.
+    Energy to 1e-12 relative, force against the curve's central difference."""
+    d, w, box, u, pos = _dimer_setup(r)
+    z = np.array([0, 1], np.int32)
+    e = nb.brute_force_edges(pos, box, d.r_cut)
+    assert len(e[0]) == 2
+    for K in (2, 3):
+        E, Ei, F = om.energy_forces(pos, z, box, e, w, d, K)
+        ref = _dimer_energy_recursion(r, w, d, K)
+        assert abs(E - ref) < 1e-12 * max(1.0, abs(E)), (K, E, ref)
+        h = 1e-5
+        dEdr = (_dimer_energy_recursion(r + h, w, d, K) - _dimer_energy_recursion(r - h, w, d, K)) / (2 * h)
+        assert np.allclose(F[1], -dEdr * u, atol=1e-8)
+        assert np.allclose(F[0], dEdr * u, atol=1e-8)
+
+
+def _mutated(w, what):
+    m = {k: v.copy() for k, v in w.items()}
+    F = m["W0"].shape[-1]
+    if what == "V_transposed":
+        m["V1"] = np.swapaxes(m["V1"], 1, 2).copy()
+        m["V2"] = np.swapaxes(m["V2"], 1, 2).copy()
+    elif what == "U2_transposed":
+        m["U2"] = np.swapaxes(m["U2"], 1, 2).copy()
+    elif what == "R1b_R2a_swapped":
+        W3 = m["W3"].copy()
+        W3[:, 2 * F:3 * F], W3[:, 3 * F:4 * F] = m["W3"][:, 3 * F:4 * F], m["W3"][:, 2 * F:3 * F]
+        m["W3"] = W3
+    elif what == "R2b_dropped":
+        m["W3"][:, 4 * F:5 * F] = 0.0
+    return m
+
+
+@pytest.mark.parametrize("what", ["V_transposed", "U2_transposed", "R1b_R2a_swapped", "R2b_dropped"])
+def test_dimer_recursion_detects_planted_mistakes(what):
+    """A mistake planted in the oracle's view of the weights (V_l applied as
+    its transpose, U_2 transposed, the R_1b / R_2a slices exchanged, the R_2b
+    message dropped) moves the two-layer energy far outside the 1e-12 the
+    recursion pins; invariances and finite differences would not see any of
+    them."""
+    d, w, box, u, pos = _dimer_setup(3.1)
+    z = np.array([0, 1], np.int32)
+    e = nb.brute_force_edges(pos, box, d.r_cut)
+    ref = _dimer_energy_recursion(3.1, w, d, 2)
+    E_bad = om.energy(pos, z, box, e, _mutated(w, what), d, 2)
+    assert abs(E_bad - ref) > 1e-8 * max(1.0, abs(ref)), (what, E_bad, ref)
+
+
 # ------------------------------------------------------- special cases --
 
 def test_zero_layers_is_embedding_readout():
