@@ -181,10 +181,12 @@ int mp_graph_partition(mp_ctx* ctx, const mp_graph* g, int n_parts, double imbal
  * vertex with the largest gain, until it holds its share of the vertex
  * weight; the best of 8 starts by cut).  No device work; for callers that
  * hold small host graphs, and for tests of this step.
- *   row_ptr [n+1] int64 (row_ptr[0] = 0), col [row_ptr[n]] int32 in 0..n-1
- *   (a symmetric graph), edge_w / vertex_w int32 or NULL (= 1).
+ *   row_ptr [n+1] int64 (row_ptr[0] = 0, non-decreasing), col [row_ptr[n]]
+ *   int32 in 0..n-1 (a symmetric graph), edge_w / vertex_w int32 >= 0 or
+ *   NULL (= 1).
  *   part_out [n] int32, written: 0..n_parts-1.
- * Errors: MP_ERR_ARG. */
+ * Errors: MP_ERR_ARG (also for a decreasing row_ptr, a column outside
+ * 0..n-1 or a negative weight; nothing is read past the arrays' ends). */
 int mp_partition_host_bisect(int n, const int64_t* row_ptr, const int32_t* col,
                              const int32_t* edge_w, const int32_t* vertex_w, int n_parts,
                              uint64_t seed, int32_t* part_out);
@@ -356,11 +358,15 @@ int mp_kernel_launches(int64_t* count);
  * result: an MD engine that reserves all of its GPU memory in a pool at
  * start-up and forbids cudaMalloc/cudaFree during a run (they synchronise
  * the device and fragment the pool), or code running where an allocation
- * failure cannot be handled.  This call sums per-atom energies exactly as
- * mp_energy_forces does for its d_energy output (FP64, fixed block tree,
- * same order) but keeps its block partial sums in a fixed array compiled
- * into the library instead of allocating scratch.  The paper has no
- * counterpart; it is a service for such callers.
+ * failure cannot be handled.  This call sums per-atom energies in FP64 with
+ * the same fixed block-tree reduction that mp_energy_forces uses for its
+ * d_energy, applied to the array as given, but keeps its block partial sums
+ * in a fixed array compiled into the library instead of allocating scratch.
+ * The result is deterministic, yet not bitwise equal to d_energy:
+ * mp_energy_forces reduces the energies in its internal cell-sorted order,
+ * while d_e_atom is in the caller's atom order, so the operands are added
+ * in a different order.  The paper has no counterpart; it is a service for
+ * such callers.
  *   d_e_atom   [n] double, device (e.g. the d_e_atom output of
  *              mp_energy_forces).
  *   d_energy   [1] double, device, written.

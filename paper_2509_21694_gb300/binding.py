@@ -245,6 +245,9 @@ def mp_partition_host_bisect(row_ptr, col, n_parts: int, seed: int = 0, edge_w=N
     n = len(row_ptr) - 1
     ew = None if edge_w is None else np.ascontiguousarray(edge_w, dtype=np.int32)
     vw = None if vertex_w is None else np.ascontiguousarray(vertex_w, dtype=np.int32)
+    m = int(row_ptr[-1]) if n >= 0 and len(row_ptr) else -1
+    if n < 0 or len(col) != m or (ew is not None and len(ew) != m) or (vw is not None and len(vw) != n):
+        raise ValueError("row_ptr, col and the weights do not describe one CSR graph")
     part = np.zeros(max(n, 1), dtype=np.int32)
     _check(_lib.mp_partition_host_bisect(n, row_ptr.ctypes.data, col.ctypes.data if len(col) else None,
                                          None if ew is None else ew.ctypes.data,
@@ -389,8 +392,15 @@ MP_NOALLOC_MAX_ATOMS = 16384 * 2048
 
 
 def mp_energy_sum_noalloc(e_atom: torch.Tensor, energy: torch.Tensor, n: int | None = None):
-    """Sum of per-atom energies into energy[0] without any device allocation."""
-    n = e_atom.shape[0] if n is None else n
+    """Sum of the first n per-atom energies (FP64, all of e_atom by default)
+    into energy[0] without any device allocation."""
+    if e_atom.dtype != torch.float64 or energy.dtype != torch.float64:
+        raise ValueError("e_atom and energy must be float64 tensors")
+    if energy.numel() < 1:
+        raise ValueError("energy needs room for one value")
+    n = e_atom.numel() if n is None else int(n)
+    if not 0 <= n <= e_atom.numel():
+        raise ValueError("n = %d outside 0..%d (the size of e_atom)" % (n, e_atom.numel()))
     _check(_lib.mp_energy_sum_noalloc(_ptr(e_atom), n, _ptr(energy), _stream()),
            "mp_energy_sum_noalloc")
 

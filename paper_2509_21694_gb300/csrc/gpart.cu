@@ -844,6 +844,9 @@ extern "C" int mp_partition_host_bisect(int n, const int64_t* row_ptr, const int
     if (n == 0) return MP_OK;
     const int64_t m = row_ptr[n];
     if (m < 0 || (m > 0 && !col)) return MP_ERR_ARG;
+    // row offsets never decrease, so every row lies inside col[0..m)
+    for (int i = 0; i < n; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return MP_ERR_ARG;
     HostGraph G;
     G.n = n;
     G.rp.assign(row_ptr, row_ptr + n + 1);
@@ -852,6 +855,10 @@ extern "C" int mp_partition_host_bisect(int n, const int64_t* row_ptr, const int
         if (G.col[e] < 0 || G.col[e] >= n) return MP_ERR_ARG;
     G.ew = edge_w ? std::vector<int32_t>(edge_w, edge_w + m) : std::vector<int32_t>(m, 1);
     G.vw = vertex_w ? std::vector<int32_t>(vertex_w, vertex_w + n) : std::vector<int32_t>(n, 1);
+    for (int32_t v : G.ew)
+        if (v < 0) return MP_ERR_ARG;
+    for (int32_t v : G.vw)
+        if (v < 0) return MP_ERR_ARG;
     std::vector<int32_t> verts(n), loc(n, -1), part(n, 0);
     std::vector<int> seen(n, 0);
     int stamp = 0;

@@ -65,3 +65,30 @@ def test_header_is_plain_c():
     r = subprocess.run([cc, "-fsyntax-only", "-Wall", "-Werror", "-x", "c",
                         os.path.join(ROOT, "include", "mpip.h")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_noalloc_sum_rejects_bad_arguments_before_any_gpu_work(lib_path):
+    """The energy sum without allocation refuses, on the host, what would make
+    its kernels read or write past a buffer: wrong dtypes, n beyond the tensor,
+    no room for the result; the C entry point refuses n < 0, null pointers and
+    n beyond its fixed scratch."""
+    import torch
+    from paper_2509_21694_gb300 import binding as mp
+    e64 = torch.zeros(8, dtype=torch.float64)
+    out = torch.zeros(1, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        mp.mp_energy_sum_noalloc(e64.float(), out)
+    with pytest.raises(ValueError):
+        mp.mp_energy_sum_noalloc(e64, out.float())
+    with pytest.raises(ValueError):
+        mp.mp_energy_sum_noalloc(e64, torch.zeros(0, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        mp.mp_energy_sum_noalloc(e64, out, n=9)
+    with pytest.raises(ValueError):
+        mp.mp_energy_sum_noalloc(e64, out, n=-1)
+    lib = mp._lib
+    dummy = ctypes.c_void_p(256)       # never dereferenced: the checks come first
+    assert lib.mp_energy_sum_noalloc(dummy, -1, dummy, None) == -1
+    assert lib.mp_energy_sum_noalloc(None, 5, dummy, None) == -1
+    assert lib.mp_energy_sum_noalloc(dummy, 5, None, None) == -1
+    assert lib.mp_energy_sum_noalloc(dummy, mp.MP_NOALLOC_MAX_ATOMS + 1, dummy, None) == -10

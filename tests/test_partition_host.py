@@ -87,3 +87,19 @@ def test_one_part_and_bad_input(mp):
     assert np.all(mp.mp_partition_host_bisect(rp, col, 1) == 0)
     with pytest.raises(mp.MPError):
         mp.mp_partition_host_bisect(rp, np.array([0, 1, 2, 9, 1, 2], np.int32), 2)
+
+
+def test_malformed_csr_and_negative_weights_are_refused(mp):
+    """A row_ptr that decreases inside, a negative vertex or edge weight: the
+    C entry point answers MP_ERR_ARG before it indexes anything."""
+    rp, col, _ = _csr(4, [(0, 1), (1, 2), (2, 3)])
+    bad = rp.copy()
+    bad[2] = bad[3] + 1                  # row 1 would end past row 2's start
+    with pytest.raises(mp.MPError):
+        mp.mp_partition_host_bisect(bad, col, 2)
+    with pytest.raises(mp.MPError):
+        mp.mp_partition_host_bisect(rp, col, 2, vertex_w=np.array([1, -1, 1, 1]))
+    with pytest.raises(mp.MPError):
+        mp.mp_partition_host_bisect(rp, col, 2, edge_w=-np.ones(len(col), np.int32))
+    with pytest.raises(ValueError):       # col shorter than row_ptr says
+        mp.mp_partition_host_bisect(rp, col[:-1], 2)

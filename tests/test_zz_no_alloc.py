@@ -38,11 +38,15 @@ def test_noalloc_energy_sum_matches_energy_forces(mp):
             got.append(float(out.item()))
             assert abs(got[-1] - E) <= F32_ENERGY * n * erms
         assert got[0] == got[1]
-        # sizes beyond the fixed scratch are refused before anything runs
+        # sizes beyond the fixed scratch are refused by the C entry point before
+        # anything runs (called directly: the Python wrapper never passes an n
+        # larger than its tensor)
         out = torch.zeros(1, dtype=torch.float64, device="cuda")
-        with pytest.raises(mp.MPError) as ex:
-            mp.mp_energy_sum_noalloc(e_atom, out, n=mp.MP_NOALLOC_MAX_ATOMS + 1)
-        assert ex.value.code == -10
+        rc = mp._lib.mp_energy_sum_noalloc(e_atom.data_ptr(), mp.MP_NOALLOC_MAX_ATOMS + 1,
+                                           out.data_ptr(), mp._stream())
+        assert rc == -10
+        torch.cuda.synchronize()
+        assert float(out.item()) == 0.0
     finally:
         mp.mp_graph_free(g)
         pot.close()
