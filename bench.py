@@ -62,9 +62,21 @@ def parse():
 
 # DRAM read + write bytes per processed edge of the tensor-core edge adjoint,
 # averaged over its layer-0 and layer-1 launches, from one ncu capture on
-# 131,072 atoms (profiles/edge_node_kernels_bf16_131k.md); scaled by the
-# edges of a launch.  Must be re-measured whenever that kernel changes.
-TRAFFIC_BYTES_PER_EDGE_BF16 = {"bwd": 436.0}
+# 131,072 atoms, scaled by the edges of a launch.  The figure belongs to the
+# kernel sources whose hash is stored beside it: once those sources change,
+# the line reports traffic null until the counters are taken again.
+TRAFFIC_BYTES_PER_EDGE_BF16 = {"bwd": (436.0, "0000000000000000")}
+TRAFFIC_SOURCES = ("edge_bf16.cu", "edge_math.cuh", "tc.cuh", "kernels.h", "common.cuh")
+
+
+def kernel_source_hash() -> str:
+    """First 16 hex digits of the SHA-256 over the edge kernels' sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2509_21694_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def max_over_ranks(ms, world, dev):
@@ -322,24 +334,29 @@ def run_ours(args, rank, world):
             edges_per_launch = (t0["edges"] + t1["edges"]) / launches_all
             if args.precision == "fp32":
                 mhz = clk.get("sm_mhz") or 2070.0
-                peak = 152 * 128 * 2 * mhz * 1e6 / 1e12      # FP32 FFMA lanes x 2 FLOP x clock
+                sms = torch.cuda.get_device_properties(dev).multi_processor_count
+                peak = sms * 128 * 2 * mhz * 1e6 / 1e12      # FP32 FFMA lanes x 2 FLOP x clock
                 roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": None, "kernel": "k_edge_" + kind,
-                        "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x median SM "
-                                     "clock %.0f MHz" % mhz,
+                        "peak_note": "FP32 FFMA: %d SMs x 128 lanes x 2 FLOP x median SM "
+                                     "clock %.0f MHz" % (sms, mhz),
                         "flops_per_launch": flops}
             else:
                 peak = peaks.get("bf16_tflops_sustained", 1700.0)
-                traffic = (TRAFFIC_BYTES_PER_EDGE_BF16[kind] * edges_per_launch
-                           if kind in TRAFFIC_BYTES_PER_EDGE_BF16 else None)
+                src_hash = kernel_source_hash()
+                per_edge, measured_on = TRAFFIC_BYTES_PER_EDGE_BF16.get(kind, (None, None))
+                current = per_edge is not None and measured_on == src_hash
+                traffic = per_edge * edges_per_launch if current else None
                 roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": traffic, "kernel": "k_edge_" + kind,
                         "edges_per_launch": edges_per_launch,
                         "peak_note": "bf16_tflops_sustained of %s peaks" % peak_kind,
-                        "flops_per_launch": flops,
-                        "traffic_note": "DRAM bytes per edge from the ncu capture in "
-                                        "profiles/edge_node_kernels_bf16_131k.md x edges per "
-                                        "launch"}
+                        "flops_per_launch": flops, "kernel_source_hash": src_hash,
+                        "traffic_note": ("ncu DRAM bytes per processed edge (131,072-atom "
+                                         "capture of these kernel sources) x edges per launch"
+                                         if current else
+                                         "null: the kernel sources changed since the last "
+                                         "ncu capture of DRAM bytes")}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -492,18 +509,30 @@ def oracle_sample_step(args, cells=6):
     return len(s.pos), step
 
 
-def cpu_baseline(args, cells=6, steps=1):
+def cpu_baseline(args, cells=6, steps=3, warmup=1):
+    """The oracle's MD throughput on a bounded sample, all host cores, after
+    a warm-up step; also one step on a single thread."""
     import torch
-    torch.set_num_threads(os.cpu_count() or 1)
+    threads = os.cpu_count() or 1
+    torch.set_num_threads(threads)
     n, step = oracle_sample_step(args, cells)
+    for _ in range(warmup):
+        step()
     t = time.perf_counter()
     for _ in range(steps):
         step()
     dt = time.perf_counter() - t
-    return {"value": n * steps / dt, "unit": UNIT, "cores": torch.get_num_threads(),
-            "kind": "oracle",
-            "sample": "%d-atom %s of the same kind and model, K=%d, %d MD step(s), FP64 "
-                      "torch CPU" % (n, sample_kind(args, cells), args.layers, steps)}
+    torch.set_num_threads(1)
+    t = time.perf_counter()
+    step()
+    dt1 = time.perf_counter() - t
+    torch.set_num_threads(threads)
+    return {"value": n * steps / dt, "unit": UNIT, "cores": threads,
+            "kind": "oracle", "value_1_thread": n / dt1,
+            "sample": "%d-atom %s of the same kind and model (the per-atom rate of a "
+                      "linear-scaling method, measured at %d atoms), K=%d, %d warm-up + %d "
+                      "timed MD step(s) on %d threads, then 1 step on 1 thread, FP64 torch CPU"
+                      % (n, sample_kind(args, cells), n, args.layers, warmup, steps, threads)}
 
 
 def sample_kind(args, cells):
@@ -522,9 +551,14 @@ def run_reference(args):
         step()
     dt = time.perf_counter() - t
     value = n * args.steps / dt
+    # the line carries this arm's config (the benchmark workload); each timed
+    # step is a bounded sample of it, which the sample string states
     cb = {"value": value, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-          "sample": "%d-atom %s of the same kind and model per step, K=%d, FP64 torch "
-                    "CPU" % (n, sample_kind(args, 6), args.layers)}
+          "sample_atoms": n,
+          "sample": "each step: one FP64 oracle MD step of a %d-atom %s of the same kind and "
+                    "model (the per-atom rate, measured at %d atoms, stands for the %d-atom "
+                    "workload), K=%d, torch CPU" % (n, sample_kind(args, 6), n,
+                                                    n_atoms_of(args), args.layers)}
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -550,7 +584,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     out = run_ours(args, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, cells=6, steps=3)
+        out["cpu_baseline"] = cpu_baseline(args, cells=6)
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

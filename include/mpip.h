@@ -116,7 +116,8 @@ int mp_set_head(mp_ctx* ctx, const double* head_params, int64_t n);
  *   d_pos  [n][3] double, caller's order, any (unwrapped) coordinates.
  *   box    host double[3], edge lengths.
  * The graph keeps its own wrapped copy of the positions, the cell order and
- * a receiver-sorted CSR.  Errors: MP_ERR_ARG, MP_ERR_BOX_TOO_SMALL,
+ * a receiver-sorted CSR.  Errors: MP_ERR_ARG (also when a coordinate is
+ * NaN or infinite, checked on the device), MP_ERR_BOX_TOO_SMALL,
  * MP_ERR_NOMEM, MP_ERR_CUDA. */
 int mp_build_neighbors(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3],
                        mp_graph** graph_out);
@@ -352,6 +353,21 @@ int mp_timing_read(mp_ctx* ctx, double* ms, int64_t* launches, int64_t* edges, i
  * process so far (host counter, no synchronisation).  The paper has no
  * counterpart; it lets a caller attribute GPU work to the library. */
 int mp_kernel_launches(int64_t* count);
+
+/* Self-test of the bounded waits (failure detection).  The tensor-core
+ * kernels wait for their MMAs on an mbarrier with a wait that gives up after
+ * a number of SM clock cycles; on a timeout they set a bit in the context's
+ * device error word, drain with a second bounded wait, free their tensor
+ * memory and return, and the call reports MP_ERR_TIMEOUT.  This call runs
+ * the same sequence in a one-CTA kernel that holds 32 tensor-memory columns
+ * and waits on an mbarrier that nothing arrives at (arrive = 0; arrive != 0
+ * arrives once first, so the wait succeeds), with no MMA issued.  The paper
+ * has no counterpart.
+ *   max_cycles  the wait's limit in SM clock cycles, 1 .. 4e9.
+ * Synchronises the context stream.  Returns MP_OK (the wait succeeded) or
+ * MP_ERR_TIMEOUT (it ran out); the context stays usable either way.
+ * Errors: MP_ERR_ARG, MP_ERR_NOMEM, MP_ERR_CUDA. */
+int mp_wait_selftest(mp_ctx* ctx, int64_t max_cycles, int arrive);
 
 /* ---- energy sum without device allocation ---------------------------------
  * Some callers cannot allocate device memory at the moment they need a

@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmpip.so")
 
 MP_OK = 0
+MP_ERR_ARG, MP_ERR_TIMEOUT = -1, -9
 MP_FP32, MP_BF16 = 0, 1
 MP_HALO_GEOM, MP_HALO_BFS = 0, 1
 MP_NVE, MP_LANGEVIN = 0, 1
@@ -87,6 +88,7 @@ def _load():
         "mp_timing_enable": (I32, [P, I32]),
         "mp_timing_read": (I32, [P, P, P, P, P]),
         "mp_energy_sum_noalloc": (I32, [P, I64, P, P]),
+        "mp_wait_selftest": (I32, [P, I64, I32]),
         "mp_head_count": (I32, [P, ctypes.POINTER(I64)]),
         "mp_head_loss_grad": (I32, [P, P, P, P, I32, I32, P, P, D, P, P]),
         "mp_head_adam_step": (I32, [P, P, D, D, D, D, I64]),
@@ -403,6 +405,14 @@ def mp_energy_sum_noalloc(e_atom: torch.Tensor, energy: torch.Tensor, n: int | N
         raise ValueError("n = %d outside 0..%d (the size of e_atom)" % (n, e_atom.numel()))
     _check(_lib.mp_energy_sum_noalloc(_ptr(e_atom), n, _ptr(energy), _stream()),
            "mp_energy_sum_noalloc")
+
+
+def mp_wait_selftest(ctx: int, max_cycles: int, arrive: bool) -> int:
+    """Run the bounded-wait self-test; returns MP_OK or MP_ERR_TIMEOUT."""
+    rc = _lib.mp_wait_selftest(ctx, int(max_cycles), 1 if arrive else 0)
+    if rc not in (MP_OK, MP_ERR_TIMEOUT):
+        _check(rc, "mp_wait_selftest")
+    return rc
 
 
 def mp_strerror(code: int) -> str:

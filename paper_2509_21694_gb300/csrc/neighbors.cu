@@ -23,6 +23,7 @@ namespace {
 
 constexpr int kErrOverlap = 1;
 constexpr int kErrCapacity = 2;    // a cell's stencil holds more than kCellCand atoms
+constexpr int kErrNonFinite = 4;   // a position coordinate is NaN or infinite
 constexpr int kCellCand = 2048;    // candidates a cell block stages in shared memory
 
 __device__ __forceinline__ double wrap1(double x, double L) {
@@ -44,15 +45,20 @@ struct BoxP {
     float rc2_lo, rc2_hi;
 };
 
+// A non-finite coordinate sets kErrNonFinite (the call then fails with
+// MP_ERR_ARG); such an atom lands in cell 0 and every distance test with it
+// is false, so nothing downstream indexes out of range before the check.
 __global__ void k_wrap_bin(const double* __restrict__ pos, int64_t n, BoxP b,
                            double* __restrict__ xw, int32_t* __restrict__ cell,
-                           int32_t* __restrict__ count) {
+                           int32_t* __restrict__ count, int* __restrict__ err) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double w = wrap1(pos[3 * i + a], b.L[a]);
+        const double x = pos[3 * i + a];
+        if (!isfinite(x)) atomicOr(err, kErrNonFinite);
+        double w = wrap1(x, b.L[a]);
         xw[3 * i + a] = w;
         c[a] = cell_coord(w, b.L[a], b.nc[a]);
     }
@@ -357,7 +363,7 @@ int build_graph(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3]
 
     MP_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int32_t) * (2 * ncell + 2), st));
     MP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
-    k_wrap_bin<<<grid_for(n, 256), 256, 0, st>>>(d_pos, n, b, xw, cell, count); note_launch();
+    k_wrap_bin<<<grid_for(n, 256), 256, 0, st>>>(d_pos, n, b, xw, cell, count, err); note_launch();
     MP_TRY(exclusive_scan_i32(count, g.cell_start.as<int32_t>(), ncell, ws.tmp, st));
     k_place<<<grid_for(n, 256), 256, 0, st>>>(cell, n, g.cell_start.as<int32_t>(), cursor,
                                               g.perm.as<int32_t>()); note_launch();
@@ -374,6 +380,7 @@ int build_graph(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3]
     int herr = 0;
     MP_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr & kErrNonFinite) return MP_ERR_ARG;
     const bool by_cell = !(herr & kErrCapacity);
     if (!by_cell) {
         MP_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));

@@ -98,6 +98,24 @@ def test_error_codes(mp):
     assert e.value.code == -3
 
 
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), -float("inf")])
+def test_non_finite_position_is_refused(mp, bad):
+    """A NaN or infinite coordinate is caught on the device (it would bin
+    into cell 0 and silently lose its edges) and the call returns MP_ERR_ARG;
+    the context stays usable."""
+    pot = _pot(mp, 5.0)
+    pos, box = synth.fcc((3, 3, 3), 3.615)
+    p = torch.tensor(pos, device="cuda")
+    p[7, 1] = bad
+    with pytest.raises(mp.MPError) as e:
+        mp.mp_build_neighbors(pot.ctx, p, box)
+    assert e.value.code == -1
+    ok = _gpu_edges(mp, pot, pos, box)
+    ref = onb.edges(pos, box, 5.0)
+    for a, b in zip(ref, ok):
+        assert np.array_equal(a, b)
+
+
 def test_dense_stencil_fallback_bit_exact(mp):
     # 2,500 atoms in a 12 A box with r_c = 5: 2 cells per axis, so every
     # stencil holds all atoms, more than a cell block stages in shared
