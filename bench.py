@@ -15,7 +15,9 @@ partitions, energy + forces through the hand-written adjoint, Verlet update.
 workload (a 6x6x6-cell block of the same lattice and model) on the host cores.
 Under torchrun every rank simulates its own independent copy of the system
 (no data-path collective, weak scaling); value = all ranks' atom-steps / the
-slowest rank's time.
+slowest rank's time.  With --shard the ranks instead share the partitions of
+one system (the paper's multi-GPU mode): one all-reduce of the FP64 forces
+and energy per step, strong scaling.
 """
 from __future__ import annotations
 
@@ -51,6 +53,10 @@ def parse():
     ap.add_argument("--partitioner", default="slabs", choices=["slabs", "graph"],
                     help="slabs: z bins with a geometric halo (the benchmark's); graph: roots "
                          "from the multilevel graph partitioner, assigned once, BFS halos")
+    ap.add_argument("--shard", action="store_true",
+                    help="the paper's multi-GPU mode: under torchrun the ranks share the "
+                         "partitions of one system (all-reduce of FP64 forces and energy each "
+                         "step; strong scaling) instead of each running its own copy")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--study", default=None, choices=["partition"],
@@ -372,6 +378,66 @@ def run_ours(args, rank, world):
     return out
 
 
+# ------------------------------------------- sharded system (strong) --
+
+def run_shard(args, rank, world):
+    """One system, its partitions spread over the ranks (contiguous slab
+    blocks); every step all-reduces the FP64 force and energy shares and
+    applies the same Verlet halves on every rank.  value = atoms x steps /
+    the slowest rank's time (strong scaling: the total work is fixed)."""
+    import torch
+    from paper_2509_21694_gb300 import build
+    build.build()
+    from paper_2509_21694_gb300 import binding as mp
+    from paper_2509_21694_gb300.sharded import LibraryOps, ShardedSystem
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s, d, w, v0 = workload(args)
+    n = len(s.pos)
+    prec = mp.MP_BF16 if args.precision == "bf16" else mp.MP_FP32
+    stream = torch.cuda.current_stream()
+    pot = mp.Potential(d, w)
+    mp.mp_set_stream(pot.ctx, stream.cuda_stream)
+    pos = torch.tensor(s.pos, device=dev)
+    vel = torch.tensor(v0, device=dev)
+    mass = torch.tensor(s.masses, device=dev)
+    sp = torch.tensor(s.species, device=dev)
+    sysm = ShardedSystem(LibraryOps(pot, sp, s.box, args.layers, prec, args.parts), args.parts)
+    forces, _ = sysm.md(pos, vel, mass, 1.0, args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = mp.mp_kernel_launches()
+    clocks = Clocks()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    forces, ledger = sysm.md(pos, vel, mass, 1.0, args.steps, forces=forces)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop(local)
+    ms_max = max_over_ranks(t0.elapsed_time(t1), world, dev)
+    import numpy as np
+    cfg = config_dict(args, n)
+    cfg["parallelism"] = "partitions %d-%d of %d on rank %d of %d" % (
+        sysm.parts[0], sysm.parts[1] - 1, args.parts, rank, world)
+    out = {"metric": METRIC, "value": n * args.steps / (ms_max * 1e-3), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "strong",
+           "vs_baseline": None, "dtype": "bf16+fp32" if args.precision == "bf16" else "fp32",
+           "data": "synthetic", "config": cfg, "e2e": None,
+           "gpu_launches": mp.mp_kernel_launches() - launches0, "clocks": clk,
+           "energy_drift_meV_per_atom_ps": drift_slope(np.array(ledger), n, 1.0),
+           "mode": "shard"}
+    pot.close()
+    return out
+
+
 # ------------------------------------------- partitioning study (GPU) --
 
 STUDY_SYSTEMS = {
@@ -582,6 +648,14 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")
+    if args.shard:
+        out = run_shard(args, rank, world)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
     out = run_ours(args, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, cells=6)

@@ -238,6 +238,28 @@ int mp_energy_forces_stress(mp_ctx* ctx, const double* d_pos, const int32_t* d_s
                             int use_head, double* d_energy, float* d_forces, double* d_e_atom,
                             double* d_stress);
 
+/* ---- multi-GPU partition distribution --------------------------------------
+ * Partitions are independent during inference (Introduction, Fig. 1c;
+ * Methods, "Global Output Integration": E = sum of root energies, F = sum
+ * over partitions of the root-energy gradients), so several processes, one
+ * per GPU, can each evaluate a contiguous range of one plan's partitions and
+ * sum their outputs.  This call evaluates partitions part_begin ..
+ * part_end - 1 of plan only and returns that range's shares in FP64:
+ *   d_energy    [1] double, written: sum of the range's root energies.
+ *   d_forces64  [n][3] double, written (caller order): sum over the range's
+ *               partitions of the gradients of their root energies (zero for
+ *               atoms in none of the range's extended sets).
+ *   d_e_atom    [n] double or NULL: the range's root energies, 0 elsewhere.
+ * Summing d_energy and d_forces64 over ranges that cover 0 .. n_parts - 1
+ * (an all-reduce across ranks) gives mp_energy_forces' energy and its forces
+ * before their FP32 rounding, up to the order of the FP64 additions.
+ * Errors: as mp_energy_forces; MP_ERR_ARG for a missing plan or a range
+ * outside 0 .. n_parts. */
+int mp_energy_forces_parts(mp_ctx* ctx, const double* d_pos, const int32_t* d_species,
+                           const mp_graph* g, const mp_plan* plan, int part_begin, int part_end,
+                           int n_layers, int precision, int use_head, double* d_energy,
+                           double* d_forces64, double* d_e_atom);
+
 /* ---- layer diagnostics ---------------------------------------------------
  * Methods, "Mean Feature Shift and Linear CKA": for the scalar features h0
  * (N x F) after each layer t = 0..n_layers of one unpartitioned evaluation
@@ -302,6 +324,20 @@ int mp_md_step(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces,
                const double* d_mass, const int32_t* d_species, int64_t n,
                const double box[3], double dt_fs, int n_steps, const mp_md_opts* opts,
                double* h_ledger);
+
+/* The two halves of a velocity-Verlet step, for callers that assemble the
+ * forces themselves (the multi-GPU path: FP64 force sums all-reduced across
+ * ranks).  Every force is rounded to FP32 first, as mp_md_step rounds its
+ * FP64 force sums, so both paths integrate the same numbers.
+ * first half:  v += dt/2 kappa F / m;  r += dt v, wrapped into the box.
+ * second half: v += dt/2 kappa F / m;  d_ke [1] double, written:
+ *              sum_i m_i |v_i|^2 / (2 kappa) (fixed-order FP64 sum).
+ *   d_forces64 [n][3] double, caller order.  Async on the context stream.
+ * Errors: MP_ERR_ARG, MP_ERR_NOMEM, MP_ERR_CUDA. */
+int mp_verlet_first_half(mp_ctx* ctx, double* d_pos, double* d_vel, const double* d_forces64,
+                         const double* d_mass, int64_t n, const double box[3], double dt_fs);
+int mp_verlet_second_half(mp_ctx* ctx, double* d_vel, const double* d_forces64,
+                          const double* d_mass, int64_t n, double dt_fs, double* d_ke);
 
 /* ---- correction head: training -------------------------------------------
  * The learned part: a per-atom head E_i^head = w2 . silu(W1 h0_i^(K) + b1)

@@ -81,6 +81,9 @@ def _load():
         "mp_plan_free": (None, [P]),
         "mp_energy_forces": (I32, [P, P, P, P, P, I32, I32, I32, P, P, P]),
         "mp_energy_forces_stress": (I32, [P, P, P, P, P, I32, I32, I32, P, P, P, P]),
+        "mp_energy_forces_parts": (I32, [P, P, P, P, P, I32, I32, I32, I32, I32, P, P, P]),
+        "mp_verlet_first_half": (I32, [P, P, P, P, P, I64, ctypes.POINTER(D), D]),
+        "mp_verlet_second_half": (I32, [P, P, P, P, I64, D, P]),
         "mp_layer_stats": (I32, [P, P, P, P, I32, I32, P, P]),
         "mp_md_step": (I32, [P, P, P, P, P, P, I64, ctypes.POINTER(D), D, I32,
                              ctypes.POINTER(mp_md_opts), P]),
@@ -304,6 +307,40 @@ def mp_energy_forces_stress(ctx: int, pos: torch.Tensor, species: torch.Tensor, 
                                         precision, int(use_head), _ptr(energy), _ptr(forces),
                                         _ptr(e_atom), _ptr(stress)), "mp_energy_forces_stress")
     return energy, forces, e_atom, stress
+
+
+def mp_energy_forces_parts(ctx: int, pos: torch.Tensor, species: torch.Tensor, g: int,
+                           plan: int, part_begin: int, part_end: int, n_layers: int,
+                           precision: int = MP_FP32, use_head: bool = False,
+                           energy: torch.Tensor | None = None,
+                           forces64: torch.Tensor | None = None,
+                           e_atom: torch.Tensor | None = None):
+    """FP64 shares (energy [1], forces [n, 3]) of partitions part_begin ..
+    part_end - 1 of ``plan``."""
+    n = pos.shape[0]
+    if energy is None:
+        energy = torch.empty(1, dtype=torch.float64, device=pos.device)
+    if forces64 is None:
+        forces64 = torch.empty(n, 3, dtype=torch.float64, device=pos.device)
+    assert energy.dtype == torch.float64 and forces64.dtype == torch.float64
+    assert forces64.numel() == 3 * n
+    _check(_lib.mp_energy_forces_parts(ctx, _ptr(pos), _ptr(species), g, plan, part_begin,
+                                       part_end, n_layers, precision, int(use_head),
+                                       _ptr(energy), _ptr(forces64), _ptr(e_atom)),
+           "mp_energy_forces_parts")
+    return energy, forces64, e_atom
+
+
+def mp_verlet_first_half(ctx: int, pos, vel, forces64, mass, box, dt: float):
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    _check(_lib.mp_verlet_first_half(ctx, _ptr(pos), _ptr(vel), _ptr(forces64), _ptr(mass),
+                                     pos.shape[0], b, dt), "mp_verlet_first_half")
+
+
+def mp_verlet_second_half(ctx: int, vel, forces64, mass, dt: float, ke: torch.Tensor):
+    assert ke.dtype == torch.float64 and ke.numel() >= 1
+    _check(_lib.mp_verlet_second_half(ctx, _ptr(vel), _ptr(forces64), _ptr(mass), vel.shape[0],
+                                      dt, _ptr(ke)), "mp_verlet_second_half")
 
 
 def mp_layer_stats(ctx: int, pos: torch.Tensor, species: torch.Tensor, g: int, n_layers: int,

@@ -415,6 +415,29 @@ int mp_energy_forces_stress(mp_ctx* ctx, const double* d_pos, const int32_t* d_s
                     use_head, d_energy, d_forces, d_e_atom, d_stress);
 }
 
+int mp_energy_forces_parts(mp_ctx* ctx, const double* d_pos, const int32_t* d_species,
+                           const mp_graph* g, const mp_plan* plan, int part_begin, int part_end,
+                           int n_layers, int precision, int use_head, double* d_energy,
+                           double* d_forces64, double* d_e_atom) {
+    if (!ctx || !g || !plan || plan->ctx != ctx || !d_forces64) return MP_ERR_ARG;
+    if (part_begin < 0 || part_begin > part_end || part_end > (int)plan->p.parts.size())
+        return MP_ERR_ARG;
+    return evaluate(ctx, d_pos, d_species, g->g, &plan->p, n_layers, precision, use_head,
+                    d_energy, nullptr, d_e_atom, nullptr, part_begin, part_end, d_forces64);
+}
+
+int mp_verlet_first_half(mp_ctx* ctx, double* d_pos, double* d_vel, const double* d_forces64,
+                         const double* d_mass, int64_t n, const double box[3], double dt_fs) {
+    if (!ctx || !box || !(dt_fs > 0)) return MP_ERR_ARG;
+    return verlet_first_half(ctx, d_pos, d_vel, d_forces64, d_mass, n, box, dt_fs);
+}
+
+int mp_verlet_second_half(mp_ctx* ctx, double* d_vel, const double* d_forces64,
+                          const double* d_mass, int64_t n, double dt_fs, double* d_ke) {
+    if (!ctx || !(dt_fs > 0)) return MP_ERR_ARG;
+    return verlet_second_half(ctx, d_vel, d_forces64, d_mass, n, dt_fs, d_ke);
+}
+
 int mp_md_step(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const double* d_mass,
                const int32_t* d_species, int64_t n, const double box[3], double dt_fs,
                int n_steps, const mp_md_opts* opts, double* h_ledger) {

@@ -216,7 +216,8 @@ int graph_partition(mp_ctx* ctx, const Graph& g, int k, double imbalance, uint64
 // evaluate.cu
 int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,
              const Plan* plan, int n_layers, int precision, int use_head, double* d_energy,
-             float* d_forces, double* d_e_atom, double* d_stress = nullptr);
+             float* d_forces, double* d_e_atom, double* d_stress = nullptr, int part_begin = 0,
+             int part_end = -1, double* d_forces64 = nullptr);
 // diagnostics.cu
 int layer_stats(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g, int K,
                 int precision, double* h_mfs, double* h_cka);
@@ -234,6 +235,10 @@ int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, DevBuf& tmp, 
 int md_run(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const double* d_mass,
            const int32_t* d_species, int64_t n, const double box[3], double dt, int n_steps,
            const mp_md_opts* o, double* h_ledger);
+int verlet_first_half(mp_ctx* ctx, double* d_pos, double* d_vel, const double* d_forces64,
+                      const double* d_mass, int64_t n, const double box[3], double dt);
+int verlet_second_half(mp_ctx* ctx, double* d_vel, const double* d_forces64,
+                       const double* d_mass, int64_t n, double dt, double* d_ke);
 
 inline int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
 

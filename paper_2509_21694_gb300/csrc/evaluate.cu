@@ -187,14 +187,20 @@ __global__ void k_scatter(int64_t n, const int32_t* __restrict__ gid,
     for (int q = 0; q < 3; ++q) f_sorted[3 * s + q] += floc[3 * l + q];
 }
 
+// Caller-order outputs: FP32 forces and/or the FP64 sums themselves (the
+// partial forces of a range of partitions, summed across ranks by the caller).
 __global__ void k_finalize(int64_t n, const int32_t* __restrict__ perm,
                            const double* __restrict__ e_sorted, const double* __restrict__ f_sorted,
-                           float* __restrict__ forces, double* __restrict__ e_atom) {
+                           float* __restrict__ forces, double* __restrict__ forces64,
+                           double* __restrict__ e_atom) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int64_t i = perm[s];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) forces[3 * i + q] = (float)f_sorted[3 * s + q];
+    for (int q = 0; q < 3; ++q) {
+        if (forces) forces[3 * i + q] = (float)f_sorted[3 * s + q];
+        if (forces64) forces64[3 * i + q] = f_sorted[3 * s + q];
+    }
     if (e_atom) e_atom[i] = e_sorted[s];
 }
 
@@ -464,12 +470,16 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
 
 int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,
              const Plan* plan, int K, int precision, int use_head, double* d_energy,
-             float* d_forces, double* d_e_atom, double* d_stress) {
+             float* d_forces, double* d_e_atom, double* d_stress, int part_begin, int part_end,
+             double* d_forces64) {
     const Model& m = ctx->model;
-    if (!d_pos || !d_species || !d_energy || !d_forces) return MP_ERR_ARG;
+    if (!d_pos || !d_species || !d_energy || (!d_forces && !d_forces64)) return MP_ERR_ARG;
     if (K < 0 || K > m.d.n_layers_full) return MP_ERR_ARG;
     if (precision != MP_FP32 && precision != MP_BF16) return MP_ERR_ARG;
     if (plan && plan->n != g.n) return MP_ERR_ARG;
+    const int n_plan_parts = plan ? (int)plan->parts.size() : 1;
+    if (part_end < 0) part_end = n_plan_parts;
+    if (part_begin < 0 || part_begin > part_end || part_end > n_plan_parts) return MP_ERR_ARG;
     cudaStream_t st = ctx->stream;
     Workspace& ws = ctx->ws;
     const int64_t n = g.n;
@@ -480,12 +490,16 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
         subs.push_back(SubSys{n, g.n_edges, g.row_ptr.as<int64_t>(), g.col.as<int32_t>(),
                               g.shift.as<int8_t>(), nullptr, nullptr, {}, {}, {}});
     } else {
-        for (const Part& P : plan->parts)
+        // partitions part_begin .. part_end - 1 (all of them by default); the
+        // energy and force sums then hold only those partitions' shares
+        for (int p = part_begin; p < part_end; ++p) {
+            const Part& P = plan->parts[p];
             if (P.n_root > 0)   // a slab without roots contributes nothing
                 subs.push_back(SubSys{P.n_ext, P.n_edges, P.row_ptr.as<int64_t>(),
                                       P.col.as<int32_t>(), P.shift.as<int8_t>(),
                                       P.gid.as<int32_t>(), P.is_root.as<uint8_t>(), P.n_le,
                                       P.e_le, P.e_same});
+        }
     }
     int64_t nmax = 0;
     for (const SubSys& s : subs) nmax = s.n > nmax ? s.n : nmax;
@@ -540,7 +554,7 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
     const EdgeConst kc = make_edge_const(m.d, g.box);
     for (const SubSys& s : subs) MP_TRY(run_subsystem(ctx, s, b, kc, K, precision, use_head));
     k_finalize<<<grid_for(n, 256), 256, 0, st>>>(n, g.perm.as<int32_t>(), b.e_sorted, b.f_sorted,
-                                                 d_forces, d_e_atom); note_launch();
+                                                 d_forces, d_forces64, d_e_atom); note_launch();
     MP_TRY(reduce_sum(b.e_sorted, n, d_energy, ws.red, st));
     if (d_stress) {
         k_stress_final<<<1, 32, 0, st>>>(b.vtot, 0.5 / (g.box[0] * g.box[1] * g.box[2]), d_stress);

@@ -96,6 +96,43 @@ __global__ void k_kick_ke(int64_t n, double* __restrict__ v, const float* __rest
     ke[i] = 0.5 * m[i] * s / kKappa;
 }
 
+// The two Verlet halves for callers that assemble the forces themselves
+// (FP64 sums of partial forces): each force is rounded to FP32 first, as the
+// single-process step rounds its FP64 force sums, so both paths integrate the
+// same numbers.
+__global__ void k_kick_drift64(int64_t n, double* __restrict__ x, double* __restrict__ v,
+                               const double* __restrict__ f, const double* __restrict__ m,
+                               double dt, double L0, double L1, double L2) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double c = 0.5 * dt * kKappa / m[i];
+    const double L[3] = {L0, L1, L2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double vv = v[3 * i + a] + c * (double)(float)f[3 * i + a];
+        v[3 * i + a] = vv;
+        double xx = __dadd_rn(x[3 * i + a], __dmul_rn(dt, vv));
+        xx = __dsub_rn(xx, __dmul_rn(L[a], floor(__ddiv_rn(xx, L[a]))));
+        if (xx >= L[a]) xx = __dsub_rn(xx, L[a]);
+        x[3 * i + a] = xx;
+    }
+}
+
+__global__ void k_kick_ke64(int64_t n, double* __restrict__ v, const double* __restrict__ f,
+                            const double* __restrict__ m, double dt, double* __restrict__ ke) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double c = 0.5 * dt * kKappa / m[i];
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double vv = v[3 * i + a] + c * (double)(float)f[3 * i + a];
+        v[3 * i + a] = vv;
+        s += vv * vv;
+    }
+    ke[i] = 0.5 * m[i] * s / kKappa;
+}
+
 __global__ void k_ledger(const double* __restrict__ pe, const double* __restrict__ ke,
                          double* __restrict__ row) {
     row[0] = *pe;
@@ -104,6 +141,32 @@ __global__ void k_ledger(const double* __restrict__ pe, const double* __restrict
 }
 
 }  // namespace
+
+int verlet_first_half(mp_ctx* ctx, double* d_pos, double* d_vel, const double* d_forces64,
+                      const double* d_mass, int64_t n, const double box[3], double dt) {
+    if (n <= 0 || !d_pos || !d_vel || !d_forces64 || !d_mass) return MP_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!(box[a] > 0)) return MP_ERR_ARG;
+    k_kick_drift64<<<grid_for(n, 256), 256, 0, ctx->stream>>>(n, d_pos, d_vel, d_forces64, d_mass,
+                                                              dt, box[0], box[1], box[2]);
+    note_launch();
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
+int verlet_second_half(mp_ctx* ctx, double* d_vel, const double* d_forces64,
+                       const double* d_mass, int64_t n, double dt, double* d_ke) {
+    if (n <= 0 || !d_vel || !d_forces64 || !d_mass || !d_ke) return MP_ERR_ARG;
+    cudaStream_t st = ctx->stream;
+    MdState& md = ctx->md;
+    MP_TRY(md.ke.reserve(sizeof(double) * n));
+    k_kick_ke64<<<grid_for(n, 256), 256, 0, st>>>(n, d_vel, d_forces64, d_mass, dt,
+                                                  md.ke.as<double>());
+    note_launch();
+    MP_TRY(reduce_sum(md.ke.as<double>(), n, d_ke, md.red, st));
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
 
 int md_run(mp_ctx* ctx, double* d_pos, double* d_vel, float* d_forces, const double* d_mass,
            const int32_t* d_species, int64_t n, const double box[3], double dt, int n_steps,
