@@ -26,7 +26,8 @@
 //      (backward) epilogue on the slice.  In the adjoint each channel forms
 //      its own share of dE_pair/dd and accumulates it over the receiver row
 //      (FP32 over a slice, compensated across slices); channels are summed
-//      once per row in FP64,
+//      once per row as FP32 two-sum pairs across a warp's lanes, then the
+//      four warps' pairs in FP64,
 //      F_k = sum_e sum_c g_c(e).
 // The adjoint of a layer first compacts each row group's edges, in order,
 // without those between two atoms of the layer's outermost hop class (their
@@ -98,8 +99,8 @@ struct alignas(1024) WgState {
     int row[SCF], col[SCF];
     int klist[KWIN];                 // adjoint: kept edges of a window (offsets from its start)
     int kwarp[4];
-    double fpart[RPG][4][3];         // per-row, per-warp force partial sums
-    double vpart[RPG][4][9];         // per-row, per-warp virial partial sums (stress)
+    float2 fpart[RPG][4][3];         // per-row, per-warp force partial sums (hi, lo)
+    float2 vpart[RPG][4][9];         // per-row, per-warp virial partial sums (stress)
     int64_t rp[RPG + 1];
     int64_t next_grp;                // next row group, fetched by the leader
     uint64_t mbar;
@@ -114,9 +115,13 @@ struct SmemTC {
 };
 static_assert(sizeof(SmemTC) + 1024 <= 232448, "shared memory of the edge kernels");
 
+// The dynamic shared memory rounded up to a 1024-byte boundary (the swizzled
+// tiles need it).  The padding is added to the __shared__ pointer itself, not
+// through an integer round trip, so the compiler still knows every access
+// below is to shared memory and emits shared-space loads and stores.
 __device__ __forceinline__ SmemTC& smem_tc(unsigned char* raw) {
-    uintptr_t p = (reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023);
-    return *reinterpret_cast<SmemTC*>(p);
+    const uint32_t pad = (1024u - (tc::smem_u32(raw) & 1023u)) & 1023u;
+    return *reinterpret_cast<SmemTC*>(raw + pad);
 }
 
 __device__ __forceinline__ void wg_sync(int g) {
@@ -325,8 +330,8 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
                 tc::mma_commit(&w.mbar);
             }
             for (int sl = 0; sl < SCF / 16; ++sl) {
-                if (!wg_wait(w, phase, g)) { alive = false; break; }
-                // prefetch the first edge's sender features
+                // prefetch the first edges' sender features before waiting for
+                // the slice's MMA (col is 0, a valid row, for slots past the end)
                 float hjc[TNLM], hjn[TNLM], hjm[TNLM];
                 // layer 0 gathers one value per edge (h0 of the sender): all 16 of
                 // the slice are requested at once, so their latency overlaps
@@ -345,6 +350,7 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
 #pragma unroll
                     for (int q = 0; q < TNLM; ++q) hjn[q] = (FIRST && q > 0) ? 0.f : __ldg(hq + q * TF);
                 }
+                if (!wg_wait(w, phase, g)) { alive = false; break; }
                 float Rb[PP::NP][8];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -419,10 +425,25 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
 
 // ------------------------------------------------------------------ adjoint --
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+// Sum over the warp's lanes of values held as unevaluated FP32 pairs
+// hi + lo, without FP64 arithmetic (whose rate on this GPU is a small
+// fraction of FP32's).  Each butterfly step adds two pairs with Knuth's
+// two-sum (s + e = a + b exactly), adds the low parts into e and
+// renormalises with a fast two-sum, so the pair keeps about 44 significant
+// bits; two-sum gives the same s and e for either operand order, so every
+// lane ends with the same pair.
+__device__ __forceinline__ void warp_sum_pair(float& hi, float& lo) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float s = __fadd_rn(hi, h2);
+        const float bb = __fsub_rn(s, hi);
+        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+        e = __fadd_rn(e, __fadd_rn(lo, l2));
+        hi = __fadd_rn(s, e);
+        lo = __fsub_rn(e, __fsub_rn(hi, s));
+    }
 }
 
 // Adjoint tile rows: row 2 e holds edge e, row 2 e + 1 its r-tangent, so a
@@ -451,9 +472,10 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
         const int64_t r0 = grp * RPG_B;
         const int nrows = (int)min((int64_t)RPG_B, a.n - r0);
         if (lt <= nrows) w.rp[lt] = a.row_ptr[r0 + lt];
-        for (int q = lt; q < RPG_B * 12; q += 128) (&w.fpart[0][0][0])[q] = 0.0;
+        for (int q = lt; q < RPG_B * 12; q += 128) (&w.fpart[0][0][0])[q] = make_float2(0.f, 0.f);
         if (STRESS)
-            for (int q = lt; q < RPG_B * 36; q += 128) (&w.vpart[0][0][0])[q] = 0.0;
+            for (int q = lt; q < RPG_B * 36; q += 128)
+                (&w.vpart[0][0][0])[q] = make_float2(0.f, 0.f);
         wg_sync(g);
         const int64_t e_beg = w.rp[0], e_end = w.rp[nrows];
         float gacc[TNLM], ak[TNLM], hk[TNLM];
@@ -487,15 +509,17 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
             }
             if (with_acc) {
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const double v = warp_sum_d((double)fk[q] - (double)fc[q]);
-                    if (lane == 0) w.fpart[lr][warp & 3][q] = v;
+                for (int q = 0; q < 3; ++q) {   // this channel's share is fk - fc
+                    float hi = fk[q], lo = -fc[q];
+                    warp_sum_pair(hi, lo);
+                    if (lane == 0) w.fpart[lr][warp & 3][q] = make_float2(hi, lo);
                 }
                 if (STRESS) {
 #pragma unroll
                     for (int q = 0; q < 9; ++q) {
-                        const double v = warp_sum_d((double)va[q]);
-                        if (lane == 0) w.vpart[lr][warp & 3][q] = v;
+                        float hi = va[q], lo = 0.f;
+                        warp_sum_pair(hi, lo);
+                        if (lane == 0) w.vpart[lr][warp & 3][q] = make_float2(hi, lo);
                     }
                 }
             }
@@ -625,7 +649,9 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                     tc::mma_commit(&w.mbar);
                 }
                 for (int sl = 0; sl < SCB / 8; ++sl) {
-                    if (!wg_wait(w, phase, g)) { alive = false; break; }
+                    // the slice's first sender gathers go out before the wait for
+                    // its MMA, so their latency overlaps it (col is 0, a valid
+                    // row, for slots past the end)
                     float ajc[TNLM], hjc[TNLM], ajn[TNLM], hjn[TNLM];
                     {
                         const int64_t jb = ((int64_t)w.col[sl * 8] * TNLM) * TF + c;
@@ -635,6 +661,7 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                             hjc[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + jb + q * TF);
                         }
                     }
+                    if (!wg_wait(w, phase, g)) { alive = false; break; }
                     // one edge of the slice: gathers of edge i in (ajc, hjc); those of
                     // edge i + 1 are fetched into (ajn, hjn) meanwhile; the caller
                     // swaps the roles of the two buffers, so nothing is copied
@@ -816,14 +843,22 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
         }
         for (int q = next; q < nrows; ++q) flush(q, false);
         wg_sync(g);
+        // the four warps' pairs of a row, summed in FP64 in a fixed order
+        auto sum4 = [](const float2 (&p)[4][3], int q) {
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v += (double)p[k][q].x + (double)p[k][q].y;
+            return v;
+        };
         if (lt < nrows * 3) {
             const int lr = lt / 3, q = lt % 3;
-            const double f = w.fpart[lr][0][q] + w.fpart[lr][1][q] + w.fpart[lr][2][q] + w.fpart[lr][3][q];
-            a.frc[(r0 + lr) * 3 + q] += f;
+            a.frc[(r0 + lr) * 3 + q] += sum4(w.fpart[lr], q);
         }
         if (STRESS && lt < nrows * 9) {
             const int lr = lt / 9, q = lt % 9;
-            const double v = w.vpart[lr][0][q] + w.vpart[lr][1][q] + w.vpart[lr][2][q] + w.vpart[lr][3][q];
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v += (double)w.vpart[lr][k][q].x + (double)w.vpart[lr][k][q].y;
             a.vir[(int64_t)q * a.vir_stride + r0 + lr] += v;
         }
         wg_sync(g);

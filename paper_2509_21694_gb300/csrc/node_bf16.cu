@@ -51,10 +51,12 @@ using NodeSmemF = NodeSmemT<5, 11>;     // forward: W0, U1, U2, V1, V2; A0, B1, 
 using NodeSmemA = NodeSmemT<3, 3>;      // adjoint, W0^T, U1^T, U2^T against gS (3 parts)
 using NodeSmemV = NodeSmemT<2, 24>;     // adjoint, V1^T, V2^T against G'_lm (3 parts each)
 
+// Dynamic shared memory rounded up to 1024 bytes by offsetting the __shared__
+// pointer itself (no integer round trip), so accesses stay shared-space.
 template <class S>
 __device__ __forceinline__ S& node_smem(unsigned char* raw) {
-    uintptr_t p = (reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023);
-    return *reinterpret_cast<S*>(p);
+    const uint32_t pad = (1024u - (tc::smem_u32(raw) & 1023u)) & 1023u;
+    return *reinterpret_cast<S*>(raw + pad);
 }
 
 // Byte offset of channels 4 q4 .. 4 q4 + 3 of atom row `row` in an operand
