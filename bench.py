@@ -136,9 +136,51 @@ def kernel_ms(timing):
     """CUDA-event milliseconds per kernel class; layer 0 of the edge kernels
     is included in edge_fwd / edge_bwd and also listed on its own."""
     out = {k: round(v["ms"], 3) for k, v in timing.items() if not k.endswith("_l0")}
-    for k in ("edge_fwd", "edge_bwd"):
+    for k in ("edge_fwd", "edge_bwd", "node_fwd", "node_bwd"):
         out[k] = round(timing[k]["ms"] + timing[k + "_l0"]["ms"], 3)
         out[k + "_layer0"] = round(timing[k + "_l0"]["ms"], 3)
+    return out
+
+
+def node_bytes_per_atom(kind: str, first: bool, last: bool, F: int = 128, nlm: int = 9) -> int:
+    """Algorithmic DRAM bytes per atom of one node-kernel launch (FP32
+    features [n][nlm][F]; every array is read or written once).
+    forward: read A (nlm F) and h (F at layer 0, whose l >= 1 inputs are zero
+    and not stored, else nlm F), write S (F) and h' (F at the last layer, else
+    nlm F).  adjoint: read dE/dh'_0 (F), S (F) and A_lm (l >= 1), write
+    alpha (nlm F); then, unless last, read dE/dh'_lm and alpha_lm and write
+    alpha_lm (l >= 1)."""
+    row, lm = 4 * F, 4 * F * (nlm - 1)
+    if kind == "fwd":
+        h_in = row if (first or last) else row + lm
+        h_out = row if last else row + lm
+        return (row + lm) + h_in + row + h_out
+    b = row + row + lm + (row + lm)
+    if not last:
+        b += 3 * lm
+    return b
+
+
+def node_hbm(timing, peak_gbs, K):
+    """HBM fraction of the node kernels from the library's CUDA-event timers:
+    algorithmic bytes (node_bytes_per_atom x atoms of each launch) over the
+    summed kernel time, for layer 0 and the later layers."""
+    out = {}
+    for kind in ("fwd", "bwd"):
+        parts = []
+        for key, first in (("node_%s_l0" % kind, True), ("node_" + kind, False)):
+            t = timing[key]
+            if not t["launches"]:
+                continue
+            # the later layers' timer holds layers 1..K-1; with K = 2 that is the
+            # last layer alone, which is the benchmark's case
+            last = (K == 1) if first else True
+            parts.append((t["atoms"] * node_bytes_per_atom(kind, first, last), t["ms"]))
+        if parts:
+            byt = sum(p[0] for p in parts)
+            ms = sum(p[1] for p in parts)
+            gbs = byt / (ms * 1e-3) / 1e9
+            out["node_" + kind] = {"gbs": gbs, "frac": gbs / peak_gbs, "bytes": byt, "ms": ms}
     return out
 
 
@@ -371,6 +413,8 @@ def run_ours(args, rank, world):
            "config": config_dict(args, n), "e2e": e2e, "gpu_launches": launches,
            "roofline": roof, "clocks": clk,
            "kernel_ms": kernel_ms(timing),
+           "hbm_kernels": (node_hbm(timing, peaks.get("hbm_gbs", 6800.0), args.layers)
+                           if args.layers == 2 else None),
            "energy_drift_meV_per_atom_ps": drift_slope(ledger, n, 1.0),
            "energy_drift_steps": int(ledger.shape[0]),
            "peaks": peak_kind}

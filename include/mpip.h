@@ -369,7 +369,9 @@ int mp_head_get(mp_ctx* ctx, double* h_params, int64_t n);
  * The paper has no counterpart; these calls let a caller measure the
  * library's kernels inside its own timed region. */
 #define MP_TIMER_NEIGHBORS   0   /* wrap, bin, cell sort, CSR count + fill     */
-#define MP_TIMER_PARTITION   1   /* root/halo flags, compaction, local CSR     */
+#define MP_TIMER_PARTITION   1   /* root/halo flags, compaction, local CSR;
+                                    also the per-edge geometry pass of the
+                                    BF16 tensor-core edge kernels             */
 #define MP_TIMER_EDGE_FWD    2   /* edge forward (basis, radial MLP, messages), */
                                  /* layers >= 1                                 */
 #define MP_TIMER_EDGE_BWD    3   /* edge adjoint (forces, sender gradients),    */
@@ -378,7 +380,9 @@ int mp_head_get(mp_ctx* ctx, double* h_params, int64_t n);
 #define MP_TIMER_NODE_BWD    5   /* node adjoint                                */
 #define MP_TIMER_EDGE_FWD_L0 6   /* edge forward of layer 0 (l >= 1 inputs zero) */
 #define MP_TIMER_EDGE_BWD_L0 7   /* edge adjoint of layer 0                     */
-#define MP_TIMER_COUNT       8
+#define MP_TIMER_NODE_FWD_L0 8   /* node update of layer 0 (timer 4: the others) */
+#define MP_TIMER_NODE_BWD_L0 9   /* node adjoint of layer 0 (timer 5: the others) */
+#define MP_TIMER_COUNT       10
 /* enable != 0 starts recording and clears the accumulators; 0 stops. */
 int mp_timing_enable(mp_ctx* ctx, int enable);
 /* Synchronises the stream, then fills host arrays of MP_TIMER_COUNT

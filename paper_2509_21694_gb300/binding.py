@@ -374,7 +374,7 @@ def mp_md_step(ctx: int, pos, vel, forces, mass, species, box, dt: float, n_step
 
 
 TIMERS = ("neighbors", "partition", "edge_fwd", "edge_bwd", "node_fwd", "node_bwd",
-          "edge_fwd_l0", "edge_bwd_l0")
+          "edge_fwd_l0", "edge_bwd_l0", "node_fwd_l0", "node_bwd_l0")
 
 
 def mp_timing_enable(ctx: int, enable: bool = True):

@@ -135,11 +135,12 @@ struct SubSys {
 struct Workspace {
     DevBuf xl, sp, H, A, S, G0, G1, alpha, floc, eatom, esum, fsum, ebuf,
         err, tmp, xw, perm_pos, pscr, pstats, red, headbuf, adam, sched, vir,
-        corder;   // partition placement: cells in Morton order [ncell], sizes, offsets
+        corder,   // partition placement: cells in Morton order [ncell], sizes, offsets
+        geo;      // tensor-core edge kernels: per edge (u_x, u_y, u_z, r) of a sub-system
     void release_all() {
         DevBuf* all[] = {&xl, &sp, &H, &A, &S, &G0, &G1, &alpha, &floc, &eatom, &esum, &fsum,
                          &ebuf, &err, &tmp, &xw, &perm_pos, &pscr, &pstats, &red, &headbuf,
-                         &adam, &sched, &vir, &corder};
+                         &adam, &sched, &vir, &corder, &geo};
         for (DevBuf* b : all) b->release();
     }
 };

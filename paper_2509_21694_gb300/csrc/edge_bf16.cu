@@ -76,10 +76,29 @@ struct alignas(1024) Tiles {
     __nv_bfloat16 W3[5][128 * 64];   // 5 x 16 KB, one 128-row tile per radial path
     __nv_bfloat16 W2[64 * 64];       // W2 (out, in), K-major
     float W1[kH * kNB + 4];          // hidden 32..63 start 4 floats later (bank offset)
+    float2 W1p[kH / 2][kNB];         // forward: rows 2p and 2p + 1 side by side
 };
 
 // Row h of W1 in shared memory.
 __device__ __forceinline__ int w1_row(int h) { return h * kNB + (h >= 32 ? 4 : 0); }
+
+// Packed FP32 pairs (two lanes of one register pair per instruction).
+__device__ __forceinline__ uint64_t f2_pack(float2 v) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(uint64_t r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+// {a.x b.x + c.x, a.y b.y + c.y}, each rounded once (fma.rn.f32x2)
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
 
 // Sigmoid from the hardware tanh (PTX tanh.approx.f32, relative error about
 // 2^-11): its absolute error, at most about 2.4e-4, stays below the BF16
@@ -187,7 +206,12 @@ __device__ __forceinline__ void tc_setup(SmemTC& s, const LayerW& wl, int np, bo
         uint4* dst = reinterpret_cast<uint4*>(s.t.W3[p]);
         for (int q = tid; q < 128 * 64 * 2 / 16; q += NTH) dst[q] = __ldg(&src[q]);
     }
-    for (int q = tid; q < kH * kNB; q += NTH) s.t.W1[w1_row(q / kNB) + q % kNB] = __ldg(&wl.W1[q]);
+    for (int q = tid; q < kH * kNB; q += NTH) {
+        const float v = __ldg(&wl.W1[q]);
+        s.t.W1[w1_row(q / kNB) + q % kNB] = v;
+        (q / kNB) & 1 ? (void)(s.t.W1p[q / kNB / 2][q % kNB].y = v)
+                      : (void)(s.t.W1p[q / kNB / 2][q % kNB].x = v);
+    }
     if ((tid & 127) == 0) {
         tc::mbar_init(&s.wg[tid >> 7].mbar, 1);
         s.wg[tid >> 7].abort = 0;
@@ -229,13 +253,12 @@ __device__ __forceinline__ int edge_geometry(const EdgeArgs& a, const int64_t* r
     }
     const int lr = find_row_t(rp, nrows, e);
     col = a.col[e];
-    float d[3];
-    edge_vector(a.x, r0 + lr, col, a.shift[e], a.k, d);
-    const float r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const float4 q = a.geo[e];   // (u, r), formed once per evaluation
+    const float r = q.w;
     const float ir = 1.f / r;
-    u4[0] = d[0] * ir;
-    u4[1] = d[1] * ir;
-    u4[2] = d[2] * ir;
+    u4[0] = q.x;
+    u4[1] = q.y;
+    u4[2] = q.z;
     u4[3] = ir;
     float env, denv;
     radial_basis<DERIV>(r, a.k, eps, deps, env, denv);
@@ -288,15 +311,22 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
                 w.col[lt] = col;
 #pragma unroll
                 for (int q = 1; q < TNLM; ++q) w.Y[lt][q - 1] = Y[q];
+                // two hidden units per packed FMA: {W1[h], W1[h+1]} x {eps, eps}
+                uint64_t ee[kNB];
+#pragma unroll
+                for (int b = 0; b < kNB; ++b) ee[b] = f2_pack(make_float2(eps[b], eps[b]));
 #pragma unroll 1
                 for (int j = 0; j < 8; ++j) {
                     float v[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        float z = 0.f;
+                    for (int q = 0; q < 8; q += 2) {
+                        uint64_t acc = f2_pack(make_float2(0.f, 0.f));
 #pragma unroll
-                        for (int b = 0; b < kNB; ++b) z = fmaf(s.t.W1[w1_row(8 * j + q) + b], eps[b], z);
-                        v[q] = z * sigmoid_fast(z);
+                        for (int b = 0; b < kNB; ++b)
+                            acc = f2_fma(f2_pack(s.t.W1p[(8 * j + q) / 2][b]), ee[b], acc);
+                        const float2 z = f2_unpack(acc);
+                        v[q] = z.x * sigmoid_fast(z.x);
+                        v[q + 1] = z.y * sigmoid_fast(z.y);
                     }
                     st_row_chunk(w.B, lt, j, v);
                 }
@@ -884,15 +914,49 @@ int launch_tc(K kernel, const EdgeArgs& a, int rpg, int num_sms, cudaStream_t st
 
 }  // namespace
 
+namespace {
+
+// Warp per row: (u, r) of each of the row's edges, in CSR order.
+__global__ void k_edge_geometry(int64_t n, const int64_t* __restrict__ row_ptr,
+                                const int32_t* __restrict__ col, const int8_t* __restrict__ shift,
+                                const double* __restrict__ x, EdgeConst k,
+                                float4* __restrict__ geo) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
+        float d[3], u[3];
+        edge_vector(x, i, col[e], shift[e], k, d);
+        const float r = edge_unit(d, u);
+        geo[e] = make_float4(u[0], u[1], u[2], r);
+    }
+}
+
+}  // namespace
+
+int launch_edge_geometry(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                         const int8_t* shift, const double* x, const EdgeConst& k, float4* geo,
+                         cudaStream_t st) {
+    if (n <= 0) return MP_OK;
+    const int wpb = 8;
+    k_edge_geometry<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, st>>>(n, row_ptr, col, shift,
+                                                                           x, k, geo);
+    note_launch();
+    MP_CUDA_TRY(cudaGetLastError());
+    return MP_OK;
+}
+
 int launch_edge_fwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int num_sms) {
-    if (!(m.d.F == TF && m.d.lmax == TLMAX) || !a.w->W3sw || !a.err || !a.sched) return MP_ERR_UNSUPPORTED;
+    if (!(m.d.F == TF && m.d.lmax == TLMAX) || !a.w->W3sw || !a.err || !a.sched || !a.geo)
+        return MP_ERR_UNSUPPORTED;
     if (a.n == 0) return MP_OK;
     return a.first ? launch_tc(k_edge_fwd_tc<true>, a, RPG_F, num_sms, st)
                    : launch_tc(k_edge_fwd_tc<false>, a, RPG_F, num_sms, st);
 }
 
 int launch_edge_bwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int num_sms) {
-    if (!(m.d.F == TF && m.d.lmax == TLMAX) || !a.w->W3sw || !a.err || !a.sched) return MP_ERR_UNSUPPORTED;
+    if (!(m.d.F == TF && m.d.lmax == TLMAX) || !a.w->W3sw || !a.err || !a.sched || !a.geo)
+        return MP_ERR_UNSUPPORTED;
     if (a.n == 0) return MP_OK;
     if (a.vir)
         return a.first ? launch_tc(k_edge_bwd_tc<true, true>, a, RPG_B, num_sms, st)

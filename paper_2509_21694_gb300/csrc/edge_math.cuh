@@ -47,6 +47,16 @@ __device__ __forceinline__ void edge_vector(const double* __restrict__ x, int64_
     d[2] = (float)__dadd_rn(__dsub_rn(x[3 * j + 2], x[3 * i + 2]), __dmul_rn((double)n2, k.L[2]));
 }
 
+// r = |d| and the unit vector u = d / r in FP32 (the reciprocal taken once).
+__device__ __forceinline__ float edge_unit(const float d[3], float u[3]) {
+    const float r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const float ir = 1.f / r;
+    u[0] = d[0] * ir;
+    u[1] = d[1] * ir;
+    u[2] = d[2] * ir;
+    return r;
+}
+
 // Envelope u(x) and du/dr.
 __device__ __forceinline__ void envelope(float r, const EdgeConst& k, float& u, float& du_dr) {
     const float x = r * k.inv_rc;

@@ -284,6 +284,7 @@ struct EvalBufs {
     double* vloc;     // stress only: per-row virial [9][n_max]; else null
     double* vsum;     // [9] one sub-system's virial
     double* vtot;     // [9] all sub-systems', in sub-system order
+    float4* geo;      // BF16: per edge (u, r) of the current sub-system
 };
 
 // Rows a pass must cover: atoms within `hops` hops of a root (a prefix of
@@ -339,6 +340,11 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
     ea.vir_stride = n;
     if (b.vloc) MP_CUDA_TRY(cudaMemsetAsync(b.vloc, 0, sizeof(double) * 9 * n, st));
     ea.sched = ctx->ws.sched.as<int>();
+    if (precision == MP_BF16) {   // edge geometry once for all of this sub-system's passes
+        ea.geo = b.geo;
+        TimerScope ts(ctx, MP_TIMER_PARTITION, ss.n_edges, n);
+        MP_TRY(launch_edge_geometry(n, ss.row_ptr, ss.col, ss.shift, x, kc, b.geo, st));
+    }
     NodeArgs na{};
     na.inv_navg = kc.inv_navg;
     na.err = ctx->ws.err.as<int>();
@@ -369,7 +375,7 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         na.first = t == 0;
         na.last = t == K - 1;
         {
-            TimerScope ts(ctx, MP_TIMER_NODE_FWD, 0, rows);
+            TimerScope ts(ctx, t == 0 ? MP_TIMER_NODE_FWD_L0 : MP_TIMER_NODE_FWD, 0, rows);
             if (precision == MP_BF16)
                 MP_TRY(launch_node_fwd_bf16(m, na, st, ctx->num_sms));
             else
@@ -417,7 +423,7 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
         na.Alpha = b.alpha;
         na.last = t == K - 1;
         {
-            TimerScope ts(ctx, MP_TIMER_NODE_BWD, 0, nrows);
+            TimerScope ts(ctx, t == 0 ? MP_TIMER_NODE_BWD_L0 : MP_TIMER_NODE_BWD, 0, nrows);
             if (precision == MP_BF16)
                 MP_TRY(launch_node_bwd_bf16(m, na, st, ctx->num_sms));
             else
@@ -501,8 +507,11 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
                                       P.e_le, P.e_same});
         }
     }
-    int64_t nmax = 0;
-    for (const SubSys& s : subs) nmax = s.n > nmax ? s.n : nmax;
+    int64_t nmax = 0, emax = 0;
+    for (const SubSys& s : subs) {
+        nmax = s.n > nmax ? s.n : nmax;
+        emax = s.n_edges > emax ? s.n_edges : emax;
+    }
     const int64_t feat = nmax * NLM * F;
 
     MP_TRY(ws.xw.reserve(sizeof(double) * 3 * n));
@@ -538,6 +547,11 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
     b.floc = ws.floc.as<double>();
     b.eloc = ws.eatom.as<double>();
     b.vloc = b.vsum = b.vtot = nullptr;
+    b.geo = nullptr;
+    if (precision == MP_BF16) {
+        MP_TRY(ws.geo.reserve(sizeof(float4) * (emax + 1)));
+        b.geo = ws.geo.as<float4>();
+    }
     if (d_stress) {
         MP_TRY(ws.vir.reserve(sizeof(double) * (9 * nmax + 18)));
         b.vloc = ws.vir.as<double>();
