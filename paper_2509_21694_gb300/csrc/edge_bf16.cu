@@ -3,10 +3,13 @@
 // first radial layer (K = 8), messages, adjoint sums and forces stay FP32 on
 // CUDA cores.  Shapes compiled: F = 128, lmax = 2, H = 64.
 //
-// A CTA holds one copy of the W2 / W3 operand tiles and runs four
-// independent warpgroups; each warpgroup owns a stream of receiver-row
-// groups, 128 tensor-memory columns, an mbarrier and a named barrier, so one
-// warpgroup's MMAs overlap the others' CUDA-core work.
+// A CTA holds one copy of the W2 / W3 operand tiles and runs independent
+// warpgroups (five in the forward, four in the adjoint, whose per-thread
+// state needs twice the registers); each warpgroup owns a stream of
+// receiver-row groups, its tensor-memory columns (96 forward, 128 adjoint),
+// an mbarrier and a named barrier, so one warpgroup's MMAs overlap the
+// others' CUDA-core work.  The geometry (unit vector and r of every edge) is
+// formed once per sub-system by k_edge_geometry and read here.
 //
 // Per super-chunk of edges of the warpgroup's rows (128 edges forward; 64
 // edges plus their r-tangents in the adjoint):
@@ -34,8 +37,9 @@
 // terms are exact zeros).  The epilogues gather the next edge's sender
 // features while the current one computes (layer 0 of the forward, which
 // gathers one value per edge, requests a whole slice's at once), and read
-// the radial outputs from tensor memory eight edges at a time (forward) or
-// per edge (adjoint).
+// the radial outputs from tensor memory four edges at a time (forward) or
+// per edge (adjoint).  The forward's first radial layer forms two hidden
+// units per packed FP32x2 FMA.
 // The MLP's hidden activations use the hardware tanh for the sigmoid: they
 // are rounded to BF16 for the next contraction anyway.
 // One thread issues the MMAs; completion is signalled through an mbarrier
@@ -49,9 +53,16 @@ namespace mp {
 namespace {
 
 constexpr int TF = 128, TLMAX = 2, TNLM = 9;
+// Adjoint: four warpgroups of 128 threads at up to 128 registers each.
 constexpr int NWG = 4;             // warpgroups per CTA
 constexpr int NTH = 128 * NWG;     // threads per CTA
 constexpr int WG_COLS = 128;       // tensor-memory columns per warpgroup (D1 and D2 share them)
+// Forward: its per-thread state is smaller, so five warpgroups (20 warps per
+// SM) hide more of the gathers' latency; D1 (64 columns) and a slice's D2
+// (at most 5 x 16 columns) share 96 columns per warpgroup.
+constexpr int NWG_F = 5;
+constexpr int NTH_F = 128 * NWG_F;
+constexpr int WG_COLS_F = 96;
 constexpr int TM_COLS = 512;       // allocated per CTA
 // Receiver rows per row group.  All warpgroups of the GPU work on
 // consecutive groups, so the group size sets the span of rows in flight and
@@ -127,20 +138,38 @@ struct alignas(1024) WgState {
 };
 
 
-struct SmemTC {
+// The forward's warpgroup state: the adjoint's fields it does not use are
+// left out so that five warpgroups fit.
+struct alignas(1024) WgStateF {
+    __nv_bfloat16 B[128 * 64];       // a1 tile, then a2 tile, of the super-chunk
+    float Y[SCF][TNLM - 1];          // Y_lm for lm = 1..8 (Y_00 = 1)
+    int row[SCF], col[SCF];
+    int64_t rp[RPG + 1];
+    int64_t next_grp;
+    uint64_t mbar;
+    int abort;
+};
+
+template <class WG, int N>
+struct SmemT {
     Tiles t;
-    WgState wg[NWG];
+    WG wg[N];
     uint32_t taddr;
 };
-static_assert(sizeof(SmemTC) + 1024 <= 232448, "shared memory of the edge kernels");
+using SmemTC = SmemT<WgState, NWG>;     // adjoint
+using SmemF = SmemT<WgStateF, NWG_F>;   // forward
+static_assert(sizeof(SmemTC) + 1024 <= 232448, "shared memory of the edge adjoint");
+static_assert(sizeof(SmemF) + 1024 <= 232448, "shared memory of the edge forward");
+static_assert(NWG * WG_COLS <= TM_COLS && NWG_F * WG_COLS_F <= TM_COLS, "tensor memory");
 
 // The dynamic shared memory rounded up to a 1024-byte boundary (the swizzled
 // tiles need it).  The padding is added to the __shared__ pointer itself, not
 // through an integer round trip, so the compiler still knows every access
 // below is to shared memory and emits shared-space loads and stores.
-__device__ __forceinline__ SmemTC& smem_tc(unsigned char* raw) {
+template <class S>
+__device__ __forceinline__ S& smem_as(unsigned char* raw) {
     const uint32_t pad = (1024u - (tc::smem_u32(raw) & 1023u)) & 1023u;
-    return *reinterpret_cast<SmemTC*>(raw + pad);
+    return *reinterpret_cast<S*>(raw + pad);
 }
 
 __device__ __forceinline__ void wg_sync(int g) {
@@ -150,8 +179,9 @@ __device__ __forceinline__ void wg_sync(int g) {
 // Row groups are handed out dynamically: each warpgroup starts at its own
 // index and then takes the next unclaimed group from a global counter, so
 // warpgroups that drew light groups keep working until the list is done.
-__device__ __forceinline__ int64_t next_group(WgState& w, const EdgeArgs& a, int g, int lt) {
-    if (lt == 0) w.next_grp = (int64_t)gridDim.x * NWG + atomicAdd(a.sched, 1);
+template <int N, class W>
+__device__ __forceinline__ int64_t next_group(W& w, const EdgeArgs& a, int g, int lt) {
+    if (lt == 0) w.next_grp = (int64_t)gridDim.x * N + atomicAdd(a.sched, 1);
     wg_sync(g);
     return w.next_grp;
 }
@@ -185,7 +215,8 @@ __device__ __forceinline__ void mma_k64(uint32_t d, const __nv_bfloat16* A, cons
 }
 
 // Bounded wait of one warpgroup on its mbarrier; uniform result.
-__device__ __forceinline__ bool wg_wait(WgState& w, uint32_t& phase, int g) {
+template <class W>
+__device__ __forceinline__ bool wg_wait(W& w, uint32_t& phase, int g) {
     const bool ok = tc::mbar_wait(&w.mbar, phase);
     if (ok)
         phase ^= 1u;
@@ -196,17 +227,18 @@ __device__ __forceinline__ bool wg_wait(WgState& w, uint32_t& phase, int g) {
     return w.abort == 0;
 }
 
-__device__ __forceinline__ void tc_setup(SmemTC& s, const LayerW& wl, int np, bool first, int tid) {
+template <int NT, class S>
+__device__ __forceinline__ void tc_setup(S& s, const LayerW& wl, int np, bool first, int tid) {
     const uint4* src2 = reinterpret_cast<const uint4*>(wl.W2sw);
     uint4* dst2 = reinterpret_cast<uint4*>(s.t.W2);
-    for (int q = tid; q < 64 * 64 * 2 / 16; q += NTH) dst2[q] = __ldg(&src2[q]);
+    for (int q = tid; q < 64 * 64 * 2 / 16; q += NT) dst2[q] = __ldg(&src2[q]);
     for (int p = 0; p < np; ++p) {
         const int blk = first ? (p == 0 ? 0 : 2 * p - 1) : p;
         const uint4* src = reinterpret_cast<const uint4*>(wl.W3sw + (size_t)blk * 128 * 64);
         uint4* dst = reinterpret_cast<uint4*>(s.t.W3[p]);
-        for (int q = tid; q < 128 * 64 * 2 / 16; q += NTH) dst[q] = __ldg(&src[q]);
+        for (int q = tid; q < 128 * 64 * 2 / 16; q += NT) dst[q] = __ldg(&src[q]);
     }
-    for (int q = tid; q < kH * kNB; q += NTH) {
+    for (int q = tid; q < kH * kNB; q += NT) {
         const float v = __ldg(&wl.W1[q]);
         s.t.W1[w1_row(q / kNB) + q % kNB] = v;
         (q / kNB) & 1 ? (void)(s.t.W1p[q / kNB / 2][q % kNB].y = v)
@@ -223,8 +255,9 @@ __device__ __forceinline__ void tc_setup(SmemTC& s, const LayerW& wl, int np, bo
     tc::fence_after_sync();
 }
 
-__device__ __forceinline__ void tc_teardown(SmemTC& s, uint32_t phase, int* err, int tid) {
-    WgState& w = s.wg[tid >> 7];
+template <class S>
+__device__ __forceinline__ void tc_teardown(S& s, uint32_t phase, int* err, int tid) {
+    auto& w = s.wg[tid >> 7];
     if (w.abort) {
         // drain: give in-flight MMAs of this warpgroup a bounded chance to land
         tc::mbar_wait(&w.mbar, phase, 20000000LL);
@@ -269,24 +302,24 @@ __device__ __forceinline__ int edge_geometry(const EdgeArgs& a, const int64_t* r
 // ------------------------------------------------------------------ forward --
 
 template <bool FIRST>
-__global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, int64_t n_groups,
-                                                        int* err) {
+__global__ void __launch_bounds__(NTH_F, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, int64_t n_groups,
+                                                          int* err) {
     using PP = TPaths<FIRST>;
     extern __shared__ unsigned char smem_raw[];
-    SmemTC& s = smem_tc(smem_raw);
+    SmemF& s = smem_as<SmemF>(smem_raw);
     const int tid = threadIdx.x, g = tid >> 7, lt = tid & 127, warp = tid >> 5;
     const int c = lt;
-    WgState& w = s.wg[g];
+    WgStateF& w = s.wg[g];
     const float* __restrict__ Hin = a.Hin;
     float* __restrict__ Aout = a.Aout;
-    tc_setup(s, wl, PP::NP, FIRST, tid);
-    const uint32_t tb = s.taddr + WG_COLS * g;
+    tc_setup<NTH_F>(s, wl, PP::NP, FIRST, tid);
+    const uint32_t tb = s.taddr + WG_COLS_F * g;
     const uint32_t tl = tb + ((uint32_t)(32 * (warp & 3)) << 16);
     uint32_t phase = 0;
     bool alive = true;
 
-    for (int64_t grp = (int64_t)blockIdx.x * NWG + g; grp < n_groups && alive;
-         grp = next_group(w, a, g, lt)) {
+    for (int64_t grp = (int64_t)blockIdx.x * NWG_F + g; grp < n_groups && alive;
+         grp = next_group<NWG_F>(w, a, g, lt)) {
         const int64_t r0 = grp * RPG_F;
         const int nrows = (int)min((int64_t)RPG_F, a.n - r0);
         if (lt <= nrows) w.rp[lt] = a.row_ptr[r0 + lt];
@@ -381,19 +414,19 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, i
                     for (int q = 0; q < TNLM; ++q) hjn[q] = (FIRST && q > 0) ? 0.f : __ldg(hq + q * TF);
                 }
                 if (!wg_wait(w, phase, g)) { alive = false; break; }
-                float Rb[PP::NP][8];
+                float Rb[PP::NP][4];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int e = sl * 16 + i;
                     const int lr = w.row[e];
                     if (lr < 0) break;
-                    if ((i & 7) == 0) {   // radial outputs of 8 edges per path at once
+                    if ((i & 3) == 0) {   // radial outputs of 4 edges per path at once
 #pragma unroll
-                        for (int q = 0; q < PP::NP; ++q) tc::tmem_ld8(tl + 16 * q + i, Rb[q]);
+                        for (int q = 0; q < PP::NP; ++q) tc::tmem_ld4(tl + 16 * q + i, Rb[q]);
                     }
                     float R[PP::NP];
 #pragma unroll
-                    for (int q = 0; q < PP::NP; ++q) R[q] = Rb[q][i & 7];
+                    for (int q = 0; q < PP::NP; ++q) R[q] = Rb[q][i & 3];
                     if (!FIRST && i + 2 < 16) {
                         const float* __restrict__ hp = Hin + ((int64_t)w.col[e + 2] * TNLM) * TF + c;
 #pragma unroll
@@ -483,7 +516,7 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
                                                         int* err) {
     using PP = TPaths<FIRST>;
     extern __shared__ unsigned char smem_raw[];
-    SmemTC& s = smem_tc(smem_raw);
+    SmemTC& s = smem_as<SmemTC>(smem_raw);
     const int tid = threadIdx.x, g = tid >> 7, lt = tid & 127, warp = tid >> 5, lane = tid & 31;
     const int c = lt;
     WgState& w = s.wg[g];
@@ -491,14 +524,14 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
     const float* __restrict__ Alpha = a.Alpha;
     const float* __restrict__ Gout = a.Gout;
     float* __restrict__ Gin = a.Gin;
-    tc_setup(s, wl, PP::NP, FIRST, tid);
+    tc_setup<NTH>(s, wl, PP::NP, FIRST, tid);
     const uint32_t tb = s.taddr + WG_COLS * g;
     const uint32_t tl = tb + ((uint32_t)(32 * (warp & 3)) << 16);
     uint32_t phase = 0;
     bool alive = true;
 
     for (int64_t grp = (int64_t)blockIdx.x * NWG + g; grp < n_groups && alive;
-         grp = next_group(w, a, g, lt)) {
+         grp = next_group<NWG>(w, a, g, lt)) {
         const int64_t r0 = grp * RPG_B;
         const int nrows = (int)min((int64_t)RPG_B, a.n - r0);
         if (lt <= nrows) w.rp[lt] = a.row_ptr[r0 + lt];
@@ -896,17 +929,17 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
     tc_teardown(s, phase, err, tid);
 }
 
-template <class K>
+template <class S, int N, class K>
 int launch_tc(K kernel, const EdgeArgs& a, int rpg, int num_sms, cudaStream_t st) {
     const int64_t groups = (a.n + rpg - 1) / rpg;
-    const size_t smem = sizeof(SmemTC) + 1024;
+    const size_t smem = sizeof(S) + 1024;
     MP_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     int64_t grid = (int64_t)num_sms;   // one CTA (one 512-column TMEM allocation) per SM
-    const int64_t need = (groups + NWG - 1) / NWG;
+    const int64_t need = (groups + N - 1) / N;
     if (grid > need) grid = need;
     MP_CUDA_TRY(cudaMemsetAsync(a.sched, 0, sizeof(int), st));
-    kernel<<<(unsigned)grid, NTH, smem, st>>>(a, *a.w, groups, a.err);
+    kernel<<<(unsigned)grid, 128 * N, smem, st>>>(a, *a.w, groups, a.err);
     note_launch();
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;
@@ -950,8 +983,8 @@ int launch_edge_fwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int
     if (!(m.d.F == TF && m.d.lmax == TLMAX) || !a.w->W3sw || !a.err || !a.sched || !a.geo)
         return MP_ERR_UNSUPPORTED;
     if (a.n == 0) return MP_OK;
-    return a.first ? launch_tc(k_edge_fwd_tc<true>, a, RPG_F, num_sms, st)
-                   : launch_tc(k_edge_fwd_tc<false>, a, RPG_F, num_sms, st);
+    return a.first ? launch_tc<SmemF, NWG_F>(k_edge_fwd_tc<true>, a, RPG_F, num_sms, st)
+                   : launch_tc<SmemF, NWG_F>(k_edge_fwd_tc<false>, a, RPG_F, num_sms, st);
 }
 
 int launch_edge_bwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int num_sms) {
@@ -959,10 +992,10 @@ int launch_edge_bwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int
         return MP_ERR_UNSUPPORTED;
     if (a.n == 0) return MP_OK;
     if (a.vir)
-        return a.first ? launch_tc(k_edge_bwd_tc<true, true>, a, RPG_B, num_sms, st)
-                       : launch_tc(k_edge_bwd_tc<false, true>, a, RPG_B, num_sms, st);
-    return a.first ? launch_tc(k_edge_bwd_tc<true, false>, a, RPG_B, num_sms, st)
-                   : launch_tc(k_edge_bwd_tc<false, false>, a, RPG_B, num_sms, st);
+        return a.first ? launch_tc<SmemTC, NWG>(k_edge_bwd_tc<true, true>, a, RPG_B, num_sms, st)
+                       : launch_tc<SmemTC, NWG>(k_edge_bwd_tc<false, true>, a, RPG_B, num_sms, st);
+    return a.first ? launch_tc<SmemTC, NWG>(k_edge_bwd_tc<true, false>, a, RPG_B, num_sms, st)
+                   : launch_tc<SmemTC, NWG>(k_edge_bwd_tc<false, false>, a, RPG_B, num_sms, st);
 }
 
 }  // namespace mp
