@@ -298,13 +298,24 @@ typedef struct {
     const int32_t* d_part;  /* NULL = z slabs; else [n] int32 device roots   */
                             /* per atom (caller order, as for                */
                             /* mp_partition_assign), halos by BFS            */
+    double skin;            /* Verlet skin, Angstrom; 0 = neighbours and     */
+                            /* partitions rebuilt after every position       */
+                            /* update.  > 0: built with r_c + skin (halos in */
+                            /* units of r_c + skin) and reused, also across  */
+                            /* calls, until an atom has moved more than      */
+                            /* skin / 2 since the build (not with d_part)    */
+    int64_t* h_builds;      /* host, may be NULL: neighbour-list builds done */
+                            /* by this call                                  */
 } mp_md_opts;
 #define MP_NVE      0
 #define MP_LANGEVIN 1
 
 /* n_steps MD steps with a = kappa F / m, kappa = 9.648533212e-3
  * Angstrom/fs^2 per eV/(Angstrom amu), rebuilding neighbours, partitions and
- * forces after every position update.
+ * forces after every position update (with a skin: neighbours and
+ * partitions only when some atom has moved more than skin / 2 since their
+ * build; the result is the same, because the list holds every pair within
+ * r_c until then and its pairs beyond r_c add exact zeros: R(r >= r_c) = 0).
  * MP_NVE: velocity Verlet (v += dt/2 a; r += dt v, wrapped; F; v += dt/2 a).
  * MP_LANGEVIN: BAOAB (Leimkuhler and Matthews): v += dt/2 a; r += dt/2 v;
  *   v = c1 v + c2 sqrt(kB T kappa / m) xi with c1 = exp(-gamma dt),
@@ -314,7 +325,10 @@ typedef struct {
  *   xi = sqrt(-2 ln(1 - u(2k))) cos(2 pi u(2k + 1)) (atom i in the caller's
  *   order, step s of this call, axis a).  The paper's MD runs use a Langevin
  *   thermostat (Results, Table 2 conditions).
- *   d_pos, d_vel  [n][3] double, updated in place (positions stay wrapped).
+ *   d_pos, d_vel  [n][3] double, updated in place (positions are wrapped
+ *                 into the box after every step, or with a skin at every
+ *                 list build only: in between they continue unwrapped, so
+ *                 they may lie outside the box by less than skin / 2).
  *   d_forces      [n][3] float: forces at the final positions on return.
  *   d_mass        [n] double amu.   dt_fs: time step.
  *   h_ledger      host double [n_steps][3] = (PE, KE, PE + KE) after each

@@ -52,7 +52,8 @@ class mp_md_opts(ctypes.Structure):
                 ("thermostat", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("temperature", ctypes.c_double), ("friction", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("step0", ctypes.c_int64),
-                ("d_part", ctypes.c_void_p)]
+                ("d_part", ctypes.c_void_p), ("skin", ctypes.c_double),
+                ("h_builds", ctypes.POINTER(ctypes.c_int64))]
 
 
 def _load():
@@ -358,18 +359,24 @@ def mp_md_step(ctx: int, pos, vel, forces, mass, species, box, dt: float, n_step
                halo_mode: int = MP_HALO_GEOM, use_head: bool = False, forces_valid: bool = False,
                check_every: int = 0, ledger: bool = True, thermostat: int = MP_NVE,
                temperature: float = 0.0, friction: float = 0.0, seed: int = 0, step0: int = 0,
-               part: torch.Tensor | None = None):
-    """``part``: per-atom roots (int32 [n] device, caller order) instead of z slabs."""
+               part: torch.Tensor | None = None, skin: float = 0.0, builds: list | None = None):
+    """``part``: per-atom roots (int32 [n] device, caller order) instead of z slabs.
+    ``skin`` (A): Verlet-skin reuse of neighbours and partitions; ``builds``, a
+    list, receives the number of list builds done by the call."""
     if part is not None:
         assert part.dtype == torch.int32 and part.is_cuda and part.is_contiguous()
+    nb = ctypes.c_int64(0)
     opts = mp_md_opts(n_layers, precision, n_parts, k_hops, halo_mode, int(use_head),
                       int(forces_valid), check_every, thermostat, 0, temperature, friction,
-                      seed, step0, _ptr(part) if part is not None else None)
+                      seed, step0, _ptr(part) if part is not None else None, float(skin),
+                      ctypes.pointer(nb))
     b = (ctypes.c_double * 3)(*[float(v) for v in box])
     led = np.zeros((max(n_steps, 1), 3), dtype=np.float64)
     _check(_lib.mp_md_step(ctx, _ptr(pos), _ptr(vel), _ptr(forces), _ptr(mass), _ptr(species),
                            pos.shape[0], b, dt, n_steps, ctypes.byref(opts),
                            led.ctypes.data if ledger else None), "mp_md_step")
+    if builds is not None:
+        builds.append(nb.value)
     return led[:n_steps]
 
 

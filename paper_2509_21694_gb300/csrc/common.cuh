@@ -96,6 +96,7 @@ struct Model {
 // Neighbour graph in cell order.  perm[s] = caller id of sorted atom s.
 struct Graph {
     int64_t n = 0, n_edges = 0;
+    double r_list = 0.0;   // the cutoff the edges were selected with (r_c, or r_c + skin)
     double box[3];
     int nc[3];
     DevBuf perm, inv, xs, cell_start, row_ptr, col, shift, scratch;
@@ -150,11 +151,17 @@ struct Workspace {
 struct MdState {
     Graph g;
     Plan plan;
-    DevBuf led, scal, ke, red;
+    DevBuf led, scal, ke, red, xref, disp;   // xref: positions at the last list build
+    // the skin list kept between calls and what it was built for
+    bool list_valid = false;
+    int64_t list_n = 0;
+    double list_r = 0.0, list_box[3] = {0, 0, 0};
+    int list_parts = 0, list_mode = 0, list_hops = 0;
     void release_all() {
         DevBuf* all[] = {&g.perm, &g.inv, &g.xs, &g.cell_start, &g.row_ptr, &g.col, &g.shift,
-                         &g.scratch, &led, &scal, &ke, &red};
+                         &g.scratch, &led, &scal, &ke, &red, &xref, &disp};
         for (DevBuf* b : all) b->release();
+        list_valid = false;
         for (Part& P : plan.parts) {
             P.gid.release(); P.is_root.release(); P.row_ptr.release(); P.col.release();
             P.shift.release();
@@ -207,7 +214,8 @@ struct mp_plan {
 namespace mp {
 
 // neighbors.cu
-int build_graph(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3], Graph& g);
+int build_graph(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3], Graph& g,
+                double r_list = 0.0);
 // partition.cu
 int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, Plan& plan,
                double* halo_factor, const int32_t* d_assign = nullptr);
@@ -218,7 +226,7 @@ int graph_partition(mp_ctx* ctx, const Graph& g, int k, double imbalance, uint64
 int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,
              const Plan* plan, int n_layers, int precision, int use_head, double* d_energy,
              float* d_forces, double* d_e_atom, double* d_stress = nullptr, int part_begin = 0,
-             int part_end = -1, double* d_forces64 = nullptr);
+             int part_end = -1, double* d_forces64 = nullptr, bool wrap_pos = true);
 // diagnostics.cu
 int layer_stats(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g, int K,
                 int precision, double* h_mfs, double* h_cka);

@@ -17,9 +17,13 @@ namespace {
 
 constexpr int kErrSpecies = 8;   // error word: a species index outside 0..S-1
 
+// Positions in cell order, wrapped into the box (wrap != 0), or as given: a
+// skin list reused between builds keeps the image shifts of its build, so
+// the positions must continue without jumps by a box length until the next
+// build wraps them.
 __global__ void k_gather_pos(const double* __restrict__ pos, const int32_t* __restrict__ species,
                              const int32_t* __restrict__ perm, int64_t n, double L0, double L1,
-                             double L2, int n_species, double* __restrict__ xs,
+                             double L2, int n_species, int wrap, double* __restrict__ xs,
                              int32_t* __restrict__ sp, int* __restrict__ err) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -28,8 +32,11 @@ __global__ void k_gather_pos(const double* __restrict__ pos, const int32_t* __re
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double x = pos[3 * i + a];
-        double w = __dsub_rn(x, __dmul_rn(L[a], floor(__ddiv_rn(x, L[a]))));
-        if (w >= L[a]) w = __dsub_rn(w, L[a]);
+        double w = x;
+        if (wrap) {
+            w = __dsub_rn(x, __dmul_rn(L[a], floor(__ddiv_rn(x, L[a]))));
+            if (w >= L[a]) w = __dsub_rn(w, L[a]);
+        }
         xs[3 * s + a] = w;
     }
     int z = species[i];
@@ -477,7 +484,7 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
 int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const Graph& g,
              const Plan* plan, int K, int precision, int use_head, double* d_energy,
              float* d_forces, double* d_e_atom, double* d_stress, int part_begin, int part_end,
-             double* d_forces64) {
+             double* d_forces64, bool wrap_pos) {
     const Model& m = ctx->model;
     if (!d_pos || !d_species || !d_energy || (!d_forces && !d_forces64)) return MP_ERR_ARG;
     if (K < 0 || K > m.d.n_layers_full) return MP_ERR_ARG;
@@ -562,7 +569,8 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
 
     k_gather_pos<<<grid_for(n, 256), 256, 0, st>>>(d_pos, d_species, g.perm.as<int32_t>(), n,
                                                    g.box[0], g.box[1], g.box[2], m.d.n_species,
-                                                   b.xs, b.sp, ws.err.as<int>()); note_launch();
+                                                   wrap_pos ? 1 : 0, b.xs, b.sp, ws.err.as<int>());
+    note_launch();
     MP_CUDA_TRY(cudaMemsetAsync(b.f_sorted, 0, sizeof(double) * 3 * n, st));
     MP_CUDA_TRY(cudaMemsetAsync(b.e_sorted, 0, sizeof(double) * n, st));
     const EdgeConst kc = make_edge_const(m.d, g.box);

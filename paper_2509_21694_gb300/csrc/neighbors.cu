@@ -316,8 +316,11 @@ __global__ void k_export(const int64_t* __restrict__ row_ptr, const int32_t* __r
 
 }  // namespace
 
-int build_graph(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3], Graph& g) {
-    const double rc = ctx->model.d.r_cut;
+int build_graph(mp_ctx* ctx, const double* d_pos, int64_t n, const double box[3], Graph& g,
+                double r_list) {
+    // the list cutoff: r_c, or r_c + skin for a list reused while atoms move
+    const double rc = r_list > 0.0 ? r_list : ctx->model.d.r_cut;
+    g.r_list = rc;
     cudaStream_t st = ctx->stream;
     if (n <= 0 || !d_pos) return MP_ERR_ARG;
     for (int a = 0; a < 3; ++a) {

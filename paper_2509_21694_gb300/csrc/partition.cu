@@ -318,7 +318,9 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
     }
     const double* xs = g.xs.as<double>();
     const double Lz = g.box[2];
-    const double rc = ctx->model.d.r_cut;
+    // geometric halo widths in units of the graph's list cutoff (r_c + skin
+    // for a skin list: every hop of the current r_c graph is an edge of it)
+    const double rc = g.r_list > 0.0 ? g.r_list : ctx->model.d.r_cut;
     // No host synchronisation until every partition is built: class counts
     // stay on the device, buffers are sized by their upper bounds (n rows;
     // a partition's edges are a subset of the graph's), and the sizes come
