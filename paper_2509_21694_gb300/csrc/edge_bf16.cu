@@ -4,9 +4,9 @@
 // CUDA cores.  Shapes compiled: F = 128, lmax = 2, H = 64.
 //
 // A CTA holds one copy of the W2 / W3 operand tiles and runs independent
-// warpgroups (five in the forward, four in the adjoint, whose per-thread
-// state needs twice the registers); each warpgroup owns a stream of
-// receiver-row groups, its tensor-memory columns (96 forward, 128 adjoint),
+// warpgroups (six or five in the forward, four in the adjoint, whose
+// per-thread state needs more registers); each warpgroup owns a stream of
+// receiver-row groups, its tensor-memory columns (80 / 96 forward, 128 adjoint),
 // an mbarrier and a named barrier, so one warpgroup's MMAs overlap the
 // others' CUDA-core work.  The geometry (unit vector and r of every edge) is
 // formed once per sub-system by k_edge_geometry and read here.
@@ -57,12 +57,16 @@ constexpr int TF = 128, TLMAX = 2, TNLM = 9;
 constexpr int NWG = 4;             // warpgroups per CTA
 constexpr int NTH = 128 * NWG;     // threads per CTA
 constexpr int WG_COLS = 128;       // tensor-memory columns per warpgroup (D1 and D2 share them)
-// Forward: its per-thread state is smaller, so five warpgroups (20 warps per
-// SM) hide more of the gathers' latency; D1 (64 columns) and a slice's D2
-// (at most 5 x 16 columns) share 96 columns per warpgroup.
-constexpr int NWG_F = 5;
-constexpr int NTH_F = 128 * NWG_F;
-constexpr int WG_COLS_F = 96;
+// Forward: its per-thread state is smaller, so more warpgroups hide more of
+// the gathers' latency: six for layer 0 (one gathered value per edge), five
+// for the later layers (96 registers); D1 (64 columns) and a slice's D2
+// (3 or 5 paths x 16 columns) share 80 or 96 columns per warpgroup.
+template <bool FIRST>
+struct FwdCfg {
+    static constexpr int NWG = FIRST ? 6 : 5;
+    static constexpr int NTH = 128 * NWG;
+    static constexpr int COLS = FIRST ? 80 : 96;
+};
 constexpr int TM_COLS = 512;       // allocated per CTA
 // Receiver rows per row group.  All warpgroups of the GPU work on
 // consecutive groups, so the group size sets the span of rows in flight and
@@ -83,8 +87,11 @@ struct TPaths {
     __host__ __device__ static constexpr int slb(int l) { return 2 * l; }
 };
 
+// Weight tiles of one layer: NP radial paths (3 at layer 0, whose l >= 1
+// inputs are zero, else 5).
+template <int NP>
 struct alignas(1024) Tiles {
-    __nv_bfloat16 W3[5][128 * 64];   // 5 x 16 KB, one 128-row tile per radial path
+    __nv_bfloat16 W3[NP][128 * 64];  // NP x 16 KB, one 128-row tile per radial path
     __nv_bfloat16 W2[64 * 64];       // W2 (out, in), K-major
     float W1[kH * kNB + 4];          // hidden 32..63 start 4 floats later (bank offset)
     float2 W1p[kH / 2][kNB];         // forward: rows 2p and 2p + 1 side by side
@@ -124,9 +131,9 @@ struct alignas(1024) WgState {
     __nv_bfloat16 B[128 * 64];       // a1 tile, then a2 tile, of the super-chunk
     float eps[SCB][kNB];
     float deps[SCB][kNB];
-    float Y[SCF][TNLM - 1];          // Y_lm for lm = 1..8 (Y_00 = 1)
+    float Y[SCB][TNLM - 1];          // Y_lm for lm = 1..8 (Y_00 = 1)
     float u[SCB][4];                 // unit vector, r
-    int row[SCF], col[SCF];
+    int row[SCB], col[SCB];
     int klist[KWIN];                 // adjoint: kept edges of a window (offsets from its start)
     int kwarp[4];
     float2 fpart[RPG][4][3];         // per-row, per-warp force partial sums (hi, lo)
@@ -150,17 +157,36 @@ struct alignas(1024) WgStateF {
     int abort;
 };
 
-template <class WG, int N>
+// Adjoint: four warpgroups at up to 128 registers, except layer 0 without
+// the stress (no sender gradients, one gathered h value per edge), whose
+// state fits 96 registers and runs five.
+template <bool FIRST, bool STRESS>
+struct BwdCfg {
+    static constexpr int NWG = (FIRST && !STRESS) ? 5 : 4;
+    static constexpr int NTH = 128 * NWG;
+    static constexpr int COLS = (FIRST && !STRESS) ? 96 : 128;
+};
+
+template <int NP, class WG, int N>
 struct SmemT {
-    Tiles t;
+    Tiles<NP> t;
     WG wg[N];
     uint32_t taddr;
 };
-using SmemTC = SmemT<WgState, NWG>;     // adjoint
-using SmemF = SmemT<WgStateF, NWG_F>;   // forward
-static_assert(sizeof(SmemTC) + 1024 <= 232448, "shared memory of the edge adjoint");
-static_assert(sizeof(SmemF) + 1024 <= 232448, "shared memory of the edge forward");
-static_assert(NWG * WG_COLS <= TM_COLS && NWG_F * WG_COLS_F <= TM_COLS, "tensor memory");
+template <bool FIRST, bool STRESS>
+using SmemB = SmemT<FIRST ? 3 : 5, WgState, BwdCfg<FIRST, STRESS>::NWG>;   // adjoint
+template <bool FIRST>
+using SmemF = SmemT<FIRST ? 3 : 5, WgStateF, FwdCfg<FIRST>::NWG>;          // forward
+template <class S>
+constexpr bool smem_fits() { return sizeof(S) + 1024 <= 232448; }
+static_assert(smem_fits<SmemB<true, false>>() && smem_fits<SmemB<false, false>>() &&
+              smem_fits<SmemB<true, true>>() && smem_fits<SmemB<false, true>>(),
+              "shared memory of the edge adjoint");
+static_assert(smem_fits<SmemF<true>>() && smem_fits<SmemF<false>>(),
+              "shared memory of the edge forward");
+static_assert(BwdCfg<true, false>::NWG * BwdCfg<true, false>::COLS <= TM_COLS &&
+              NWG * WG_COLS <= TM_COLS && FwdCfg<true>::NWG * FwdCfg<true>::COLS <= TM_COLS &&
+              FwdCfg<false>::NWG * FwdCfg<false>::COLS <= TM_COLS, "tensor memory");
 
 // The dynamic shared memory rounded up to a 1024-byte boundary (the swizzled
 // tiles need it).  The padding is added to the __shared__ pointer itself, not
@@ -302,24 +328,25 @@ __device__ __forceinline__ int edge_geometry(const EdgeArgs& a, const int64_t* r
 // ------------------------------------------------------------------ forward --
 
 template <bool FIRST>
-__global__ void __launch_bounds__(NTH_F, 1) k_edge_fwd_tc(EdgeArgs a, LayerW wl, int64_t n_groups,
-                                                          int* err) {
+__global__ void __launch_bounds__(FwdCfg<FIRST>::NTH, 1)
+    k_edge_fwd_tc(EdgeArgs a, LayerW wl, int64_t n_groups, int* err) {
     using PP = TPaths<FIRST>;
+    using Cfg = FwdCfg<FIRST>;
     extern __shared__ unsigned char smem_raw[];
-    SmemF& s = smem_as<SmemF>(smem_raw);
+    SmemF<FIRST>& s = smem_as<SmemF<FIRST>>(smem_raw);
     const int tid = threadIdx.x, g = tid >> 7, lt = tid & 127, warp = tid >> 5;
     const int c = lt;
     WgStateF& w = s.wg[g];
     const float* __restrict__ Hin = a.Hin;
     float* __restrict__ Aout = a.Aout;
-    tc_setup<NTH_F>(s, wl, PP::NP, FIRST, tid);
-    const uint32_t tb = s.taddr + WG_COLS_F * g;
+    tc_setup<Cfg::NTH>(s, wl, PP::NP, FIRST, tid);
+    const uint32_t tb = s.taddr + Cfg::COLS * g;
     const uint32_t tl = tb + ((uint32_t)(32 * (warp & 3)) << 16);
     uint32_t phase = 0;
     bool alive = true;
 
-    for (int64_t grp = (int64_t)blockIdx.x * NWG_F + g; grp < n_groups && alive;
-         grp = next_group<NWG_F>(w, a, g, lt)) {
+    for (int64_t grp = (int64_t)blockIdx.x * Cfg::NWG + g; grp < n_groups && alive;
+         grp = next_group<Cfg::NWG>(w, a, g, lt)) {
         const int64_t r0 = grp * RPG_F;
         const int nrows = (int)min((int64_t)RPG_F, a.n - r0);
         if (lt <= nrows) w.rp[lt] = a.row_ptr[r0 + lt];
@@ -512,11 +539,12 @@ __device__ __forceinline__ void warp_sum_pair(float& hi, float& lo) {
 // Adjoint tile rows: row 2 e holds edge e, row 2 e + 1 its r-tangent, so a
 // 16-row slice is 8 edges and D2 columns (2 i, 2 i + 1) are (R, dR/dr).
 template <bool FIRST, bool STRESS>
-__global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, int64_t n_groups,
-                                                        int* err) {
+__global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
+    k_edge_bwd_tc(EdgeArgs a, LayerW wl, int64_t n_groups, int* err) {
     using PP = TPaths<FIRST>;
+    using Cfg = BwdCfg<FIRST, STRESS>;
     extern __shared__ unsigned char smem_raw[];
-    SmemTC& s = smem_as<SmemTC>(smem_raw);
+    auto& s = smem_as<SmemB<FIRST, STRESS>>(smem_raw);
     const int tid = threadIdx.x, g = tid >> 7, lt = tid & 127, warp = tid >> 5, lane = tid & 31;
     const int c = lt;
     WgState& w = s.wg[g];
@@ -524,14 +552,14 @@ __global__ void __launch_bounds__(NTH, 1) k_edge_bwd_tc(EdgeArgs a, LayerW wl, i
     const float* __restrict__ Alpha = a.Alpha;
     const float* __restrict__ Gout = a.Gout;
     float* __restrict__ Gin = a.Gin;
-    tc_setup<NTH>(s, wl, PP::NP, FIRST, tid);
-    const uint32_t tb = s.taddr + WG_COLS * g;
+    tc_setup<Cfg::NTH>(s, wl, PP::NP, FIRST, tid);
+    const uint32_t tb = s.taddr + Cfg::COLS * g;
     const uint32_t tl = tb + ((uint32_t)(32 * (warp & 3)) << 16);
     uint32_t phase = 0;
     bool alive = true;
 
-    for (int64_t grp = (int64_t)blockIdx.x * NWG + g; grp < n_groups && alive;
-         grp = next_group<NWG>(w, a, g, lt)) {
+    for (int64_t grp = (int64_t)blockIdx.x * Cfg::NWG + g; grp < n_groups && alive;
+         grp = next_group<Cfg::NWG>(w, a, g, lt)) {
         const int64_t r0 = grp * RPG_B;
         const int nrows = (int)min((int64_t)RPG_B, a.n - r0);
         if (lt <= nrows) w.rp[lt] = a.row_ptr[r0 + lt];
@@ -983,8 +1011,10 @@ int launch_edge_fwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int
     if (!(m.d.F == TF && m.d.lmax == TLMAX) || !a.w->W3sw || !a.err || !a.sched || !a.geo)
         return MP_ERR_UNSUPPORTED;
     if (a.n == 0) return MP_OK;
-    return a.first ? launch_tc<SmemF, NWG_F>(k_edge_fwd_tc<true>, a, RPG_F, num_sms, st)
-                   : launch_tc<SmemF, NWG_F>(k_edge_fwd_tc<false>, a, RPG_F, num_sms, st);
+    return a.first
+               ? launch_tc<SmemF<true>, FwdCfg<true>::NWG>(k_edge_fwd_tc<true>, a, RPG_F, num_sms, st)
+               : launch_tc<SmemF<false>, FwdCfg<false>::NWG>(k_edge_fwd_tc<false>, a, RPG_F,
+                                                            num_sms, st);
 }
 
 int launch_edge_bwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int num_sms) {
@@ -992,10 +1022,14 @@ int launch_edge_bwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int
         return MP_ERR_UNSUPPORTED;
     if (a.n == 0) return MP_OK;
     if (a.vir)
-        return a.first ? launch_tc<SmemTC, NWG>(k_edge_bwd_tc<true, true>, a, RPG_B, num_sms, st)
-                       : launch_tc<SmemTC, NWG>(k_edge_bwd_tc<false, true>, a, RPG_B, num_sms, st);
-    return a.first ? launch_tc<SmemTC, NWG>(k_edge_bwd_tc<true, false>, a, RPG_B, num_sms, st)
-                   : launch_tc<SmemTC, NWG>(k_edge_bwd_tc<false, false>, a, RPG_B, num_sms, st);
+        return a.first ? launch_tc<SmemB<true, true>, BwdCfg<true, true>::NWG>(
+                             k_edge_bwd_tc<true, true>, a, RPG_B, num_sms, st)
+                       : launch_tc<SmemB<false, true>, BwdCfg<false, true>::NWG>(
+                             k_edge_bwd_tc<false, true>, a, RPG_B, num_sms, st);
+    return a.first ? launch_tc<SmemB<true, false>, BwdCfg<true, false>::NWG>(
+                         k_edge_bwd_tc<true, false>, a, RPG_B, num_sms, st)
+                   : launch_tc<SmemB<false, false>, BwdCfg<false, false>::NWG>(
+                         k_edge_bwd_tc<false, false>, a, RPG_B, num_sms, st);
 }
 
 }  // namespace mp
