@@ -256,18 +256,39 @@ class Clocks:
 
 # ----------------------------------------------------------- roofline --
 
-def edge_flops(kind: str, F: int, lmax: int, first: bool) -> float:
-    """Algorithmic FLOPs per directed edge (2 per multiply-add)."""
+# Algorithmic FP32 (CUDA-core) FLOPs per directed edge and channel of the
+# BF16 edge kernels' epilogues, counted from the formulas as the kernels
+# evaluate them (a multiply-add = 2, a multiply or add = 1):
+#   adjoint, layer >= 1 (symmetric pair: both directions of the edge):
+#     Y-weighted sums of both sides' adjoints (sk_l, sj_l)           32
+#     sender gradient dE/dh_k of the reverse edge                     22
+#     dE/dR_q of both directions contracted with dR_q/dr              50
+#     dE/dY_lm = R_la (ak_lm hj0 -+ aj_lm hk0)                         28
+#     dY/du contraction (v) and the pair-gradient share t u + v / r   43
+#                                                            total   175
+#   adjoint, layer 0 (no l >= 1 inputs): P_lm 24, P.Y 16, dE/dY 8,
+#     dR contraction 8, dY/du and pair gradient 43             total    99
+#   forward, layer >= 1: A0 2, l = 1: 13, l = 2: 21            total    36
+#   forward, layer 0:                                          total    20
+# plus the first radial layer (K = 8 -> H = 64, FP32) per edge: value and
+# r-tangent in the adjoint (2 x 8 x 64 multiply-adds), value in the forward.
+FP32_FLOPS_PER_CHANNEL = {("bwd", False): 175, ("bwd", True): 99,
+                          ("fwd", False): 36, ("fwd", True): 20}
+
+
+def edge_fp32_flops(kind: str, F: int, first: bool) -> float:
     H, NB = 64, 8
+    rows = 2 if kind == "bwd" else 1
+    return float(FP32_FLOPS_PER_CHANNEL[(kind, first)] * F + rows * 2 * NB * H)
+
+
+def edge_tensor_flops(kind: str, F: int, lmax: int, first: bool) -> float:
+    """BF16 tensor-core FLOPs per edge: radial-MLP layers 2 and 3 (H x H and
+    H x paths F), for the value row and, in the adjoint, its r-tangent row."""
+    H = 64
     n_paths = (1 + lmax) if first else (1 + 2 * lmax)
-    mlp = NB * H + H * H + H * n_paths * F                       # one MLP pass, MACs
-    if kind == "fwd":
-        msg = F * (1 + sum((1 + (2 * l + 1) * (1 if first else 2)) for l in range(1, lmax + 1)))
-        return 2.0 * (mlp + msg)
-    # adjoint: MLP value + tangent, dR . dE/dR, sender gradients, dE/dR, dE/dY
-    epi = F * (2 * n_paths + (0 if first else 1 + sum(2 * (2 * l + 1) for l in range(1, lmax + 1)))
-               + sum(4 * (2 * l + 1) for l in range(1, lmax + 1)) + 2)
-    return 2.0 * (2 * mlp + epi)
+    rows = 2 if kind == "bwd" else 1
+    return 2.0 * rows * (H * H + H * n_paths * F)
 
 
 def load_peaks():
@@ -381,31 +402,54 @@ def run_ours(args, rank, world):
         t0, t1 = timing[dom + "_l0"], timing[dom]
         launches_all = t0["launches"] + t1["launches"]
         if launches_all:
-            flops = (t0["edges"] * edge_flops(kind, 128, 2, True) +
-                     t1["edges"] * edge_flops(kind, 128, 2, False)) / launches_all
             dur = (t0["ms"] + t1["ms"]) / launches_all * 1e-3
-            achieved = flops / dur / 1e12
             edges_per_launch = (t0["edges"] + t1["edges"]) / launches_all
+            mhz = clk.get("sm_mhz") or 2070.0
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            alu_peak = sms * 128 * 2 * mhz * 1e6 / 1e12   # FP32 lanes x 2 FLOP x clock
             if args.precision == "fp32":
-                mhz = clk.get("sm_mhz") or 2070.0
-                sms = torch.cuda.get_device_properties(dev).multi_processor_count
-                peak = sms * 128 * 2 * mhz * 1e6 / 1e12      # FP32 FFMA lanes x 2 FLOP x clock
-                roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None, "kernel": "k_edge_" + kind,
-                        "peak_note": "FP32 FFMA: %d SMs x 128 lanes x 2 FLOP x median SM "
+                # every FLOP of the FP32 path runs on the CUDA cores: the radial
+                # MLP (all three layers) and the epilogue
+                flops = sum(t["edges"] * (edge_tensor_flops(kind, 128, 2, first) +
+                                          edge_fp32_flops(kind, 128, first))
+                            for t, first in ((t0, True), (t1, False))) / launches_all
+                achieved = flops / dur / 1e12
+                roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak,
+                        "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                        "kernel": "k_edge_" + kind,
+                        "peak_note": "FP32: %d SMs x 128 lanes x 2 FLOP x median SM "
                                      "clock %.0f MHz" % (sms, mhz),
                         "flops_per_launch": flops}
             else:
-                peak = peaks.get("bf16_tflops_sustained", 1700.0)
+                # two resources: the tensor pipe (radial layers 2 and 3) and the
+                # FP32 pipe (radial layer 1 and the per-channel epilogue); the
+                # bound is the one whose algorithmic work takes longer at peak
+                tfl = (t0["edges"] * edge_tensor_flops(kind, 128, 2, True) +
+                       t1["edges"] * edge_tensor_flops(kind, 128, 2, False)) / launches_all
+                afl = (t0["edges"] * edge_fp32_flops(kind, 128, True) +
+                       t1["edges"] * edge_fp32_flops(kind, 128, False)) / launches_all
+                tpk = peaks.get("bf16_tflops_sustained", 1700.0)
                 src_hash = kernel_source_hash()
                 per_edge, measured_on = TRAFFIC_BYTES_PER_EDGE_BF16.get(kind, (None, None))
                 current = per_edge is not None and measured_on == src_hash
                 traffic = per_edge * edges_per_launch if current else None
-                roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": traffic, "kernel": "k_edge_" + kind,
-                        "edges_per_launch": edges_per_launch,
-                        "peak_note": "bf16_tflops_sustained of %s peaks" % peak_kind,
-                        "flops_per_launch": flops, "kernel_source_hash": src_hash,
+                views = {
+                    "tensor": {"achieved": tfl / dur / 1e12, "peak": tpk,
+                               "frac": tfl / dur / 1e12 / tpk, "flops_per_launch": tfl,
+                               "ideal_ms": tfl / (tpk * 1e12) * 1e3,
+                               "peak_note": "bf16_tflops_sustained of %s peaks" % peak_kind},
+                    "alu": {"achieved": afl / dur / 1e12, "peak": alu_peak,
+                            "frac": afl / dur / 1e12 / alu_peak, "flops_per_launch": afl,
+                            "ideal_ms": afl / (alu_peak * 1e12) * 1e3,
+                            "peak_note": "FP32: %d SMs x 128 lanes x 2 FLOP x median SM "
+                                         "clock %.0f MHz" % (sms, mhz)}}
+                bound = max(views, key=lambda k: views[k]["ideal_ms"])
+                v = views[bound]
+                roof = {"bound": bound, "achieved": v["achieved"], "peak": v["peak"],
+                        "unit": "TFLOP/s", "frac": v["frac"], "traffic": traffic,
+                        "kernel": "k_edge_" + kind, "edges_per_launch": edges_per_launch,
+                        "launch_ms": dur * 1e3, "views": views,
+                        "kernel_source_hash": src_hash,
                         "traffic_note": ("ncu DRAM bytes per processed edge (131,072-atom "
                                          "capture of these kernel sources) x edges per launch"
                                          if current else
