@@ -671,8 +671,17 @@ def oracle_sample_step(args, cells=6):
 
 
 def cpu_baseline(args, cells=6, steps=3, warmup=1):
-    """The oracle's MD throughput on a bounded sample, all host cores, after
-    a warm-up step; also one step on a single thread."""
+    """The oracle's MD throughput on a bounded sample, timed in a fresh
+    process (started with spawn, so it inherits nothing of this process's GPU
+    state or thread settings), all host cores after a warm-up step, then one
+    step on a single thread."""
+    import multiprocessing as mpr
+    with mpr.get_context("spawn").Pool(1) as pool:
+        return pool.apply(_cpu_baseline_child, (vars(args), cells, steps, warmup))
+
+
+def _cpu_baseline_child(argd, cells, steps, warmup):
+    args = argparse.Namespace(**argd)
     import torch
     threads = os.cpu_count() or 1
     torch.set_num_threads(threads)
