@@ -47,8 +47,9 @@ def parse():
     ap.add_argument("--layers", type=int, default=2)
     ap.add_argument("--parts", type=int, default=8)
     ap.add_argument("--cells", type=int, default=64, help="FCC cells per axis")
-    ap.add_argument("--structure", default="fcc", choices=["fcc", "liquid"],
-                    help="fcc: FCC Cu (cells^3 x 4 atoms); liquid: 3-species random liquid")
+    ap.add_argument("--structure", default="fcc", choices=["fcc", "liquid", "alloy"],
+                    help="fcc: FCC Cu (cells^3 x 4 atoms); liquid: 3-species random liquid; "
+                         "alloy: random Cu/Ni FCC alloy (a = 3.6 A, 0.08 A displacements)")
     ap.add_argument("--atoms", type=int, default=32000, help="atoms of the liquid")
     ap.add_argument("--partitioner", default="slabs", choices=["slabs", "graph"],
                     help="slabs: z bins with a geometric halo (the benchmark's); graph: roots "
@@ -61,6 +62,9 @@ def parse():
                     help="Verlet skin in A: neighbours and partitions built with r_c + skin and "
                          "reused until an atom has moved more than skin / 2 (0 = rebuilt every "
                          "step, the benchmark's definition)")
+    ap.add_argument("--sample-cells", type=int, default=6,
+                    help="cells per axis of the oracle's sample block (FCC kinds; the "
+                         "liquid sample has 4 x cells^3 atoms)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--study", default=None, choices=["partition"],
@@ -125,6 +129,12 @@ def system_and_model(args, cells=None, atoms=None):
         s = synth.liquid3(n=atoms or args.atoms, seed=2)
         d = synth.model_liquid(n_layers_full=6)
         d.rep_eps = 0.3
+        w = synth.make_weights(d, 1)
+    elif args.structure == "alloy":
+        # the depth-comparison alloy: 50/50 Cu/Ni on an FCC lattice
+        c = cells or args.cells
+        s = synth.alloy_fcc(cells=(c,) * 3)
+        d = synth.model_alloy(n_layers_full=6)
         w = synth.make_weights(d, 1)
     else:
         # thermal-scale random displacements (0.05 A) so the start is not a
@@ -200,8 +210,8 @@ def n_atoms_of(args):
 
 
 def config_dict(args, n_atoms):
-    name = "liquid3-%d-md-600K" % n_atoms if args.structure == "liquid" else \
-        "fcc-cu-%d-md-600K" % n_atoms
+    name = {"liquid": "liquid3-%d-md-600K", "alloy": "fcc-cuni-alloy-%d-md-600K"}.get(
+        args.structure, "fcc-cu-%d-md-600K") % n_atoms
     return {"workload": name, "atoms": n_atoms,
             "layers_K": args.layers, "layers_full": 6, "F": 128, "lmax": 2, "r_cut_A": 6.0,
             "partitions": args.parts, "halo_A": 6.0 * args.layers,
@@ -706,14 +716,16 @@ def _cpu_baseline_child(argd, cells, steps, warmup):
 
 
 def sample_kind(args, cells):
-    return ("liquid cell" if args.structure == "liquid"
-            else "FCC Cu block (%d^3 cells)" % cells)
+    if args.structure == "liquid":
+        return "liquid cell"
+    return ("FCC Cu/Ni alloy block (%d^3 cells)" if args.structure == "alloy"
+            else "FCC Cu block (%d^3 cells)") % cells
 
 
 def run_reference(args):
     import torch
     torch.set_num_threads(os.cpu_count() or 1)
-    n, step = oracle_sample_step(args)
+    n, step = oracle_sample_step(args, cells=args.sample_cells)
     for _ in range(args.warmup):
         step()
     t = time.perf_counter()
@@ -727,7 +739,7 @@ def run_reference(args):
           "sample_atoms": n,
           "sample": "each step: one FP64 oracle MD step of a %d-atom %s of the same kind and "
                     "model (the per-atom rate, measured at %d atoms, stands for the %d-atom "
-                    "workload), K=%d, torch CPU" % (n, sample_kind(args, 6), n,
+                    "workload), K=%d, torch CPU" % (n, sample_kind(args, args.sample_cells), n,
                                                     n_atoms_of(args), args.layers)}
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
