@@ -34,7 +34,10 @@ stress (energy_forces_stress)
 
 Parity pins (tests/test_oracle_*.py): Bessel and envelope closed forms and
 envelope derivatives at x = 1, spherical-harmonic norms, parity and addition
-theorem, the analytic dimer energy curve, K = 0 special case, translation /
+theorem, the analytic dimer energy curve, a heteronuclear dimer through two
+and three lmax = 2 layers written as a channel-vector recursion (pins
+R_lb h^l_j, V_l, U_2 and the R slice order), pairs beyond r_c adding
+nothing (the Verlet-skin reading), K = 0 special case, translation /
 rotation / permutation invariance, perfect-FCC zero forces, supercell
 replication, sum F = 0 and central finite differences of the energy; for the
 stress: central differences over real rescalings of the cell, the closed-form
