@@ -42,3 +42,26 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(42.0, 1, torch.device("cpu")) == 42.0
     assert bench.weak_value(1, 100, 5, 500.0) == pytest.approx(1000.0)
+
+
+def test_roofline_accounting():
+    """The per-edge work the roofline divides by: the tensor part is the two
+    BF16 radial layers (value row, plus the r-tangent row in the adjoint),
+    the FP32 part the per-channel epilogue plus the first radial layer; the
+    node kernels' bytes are each array read or written once."""
+    import bench
+    F, H = 128, 64
+    assert bench.edge_tensor_flops("fwd", F, 2, False) == 2 * (H * H + H * 5 * F)
+    assert bench.edge_tensor_flops("bwd", F, 2, True) == 2 * 2 * (H * H + H * 3 * F)
+    assert bench.edge_fp32_flops("bwd", F, False) == 175 * F + 2 * 2 * 8 * H
+    assert bench.edge_fp32_flops("fwd", F, True) == 20 * F + 2 * 8 * H
+    row, lm = 4 * F, 4 * F * 8
+    # forward, layer 0 of two: read A (9 rows) and h0, write S and h' (9 rows)
+    assert bench.node_bytes_per_atom("fwd", True, False) == (row + lm) + row + row + (row + lm)
+    # adjoint of the last layer: read dE/dh'_0, S and A_lm, write alpha
+    assert bench.node_bytes_per_atom("bwd", False, True) == row + row + lm + (row + lm)
+    # the adjoint's FP32 work at the FP32 peak outlasts its BF16 work at the
+    # tensor peak, so its roofline bound is the FP32 pipe
+    t_tensor = bench.edge_tensor_flops("bwd", F, 2, False) / 1708e12
+    t_alu = bench.edge_fp32_flops("bwd", F, False) / (152 * 128 * 2 * 2.07e9)
+    assert t_alu > 2 * t_tensor
