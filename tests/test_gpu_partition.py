@@ -142,4 +142,23 @@ def test_partitioned_equals_unpartitioned_three_layers(mp, precision):
                                                          np.abs(b - a).max() / frms))
         assert np.abs(b - a).max() <= 2e-6 * frms, np.abs(b - a).max() / frms
         assert np.array_equal(e0.cpu().numpy(), e1.cpu().numpy())
+    # the same comparison on the FP64 force sums before their FP32 rounding
+    # (one plan of one partition = the unpartitioned system): the difference
+    # is already there, so it comes from the FP32 arithmetic on each
+    # partition's partial adjoints, not from the output rounding
+    g = mp.mp_build_neighbors(pot.ctx, pos, s.box)
+    f64 = {}
+    try:
+        for P in (1, 4):
+            plan, _ = mp.mp_partition(pot.ctx, g, P, 3, mp.MP_HALO_GEOM)
+            _, f, _ = mp.mp_energy_forces_parts(pot.ctx, pos, sp, g, plan, 0, P, 3, prec)
+            torch.cuda.synchronize()
+            f64[P] = f.cpu().numpy()
+            mp.mp_plan_free(plan)
+    finally:
+        mp.mp_graph_free(g)
+    frms = np.sqrt((f64[1] ** 2).mean())
+    d64 = np.abs(f64[4] - f64[1]).max() / frms
+    print("K=3 %s FP64 sums: max|dF| / F_rms = %.3g" % (precision, d64))
+    assert d64 <= 2e-6
     pot.close()
