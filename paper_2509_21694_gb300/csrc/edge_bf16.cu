@@ -977,17 +977,66 @@ int launch_tc(K kernel, const EdgeArgs& a, int rpg, int num_sms, cudaStream_t st
 
 namespace {
 
-// Warp per row: (u, r) of each of the row's edges, in CSR order.
+// Every position coordinate as an unevaluated FP32 pair hi + lo (hi = the
+// FP32 rounding of x, lo = the rounding of the remainder: about 48
+// significant bits, more than the edge vector needs).
+__global__ void k_split_positions(int64_t n, const double* __restrict__ x,
+                                  float4* __restrict__ hi, float4* __restrict__ lo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float h[3], l[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double v = x[3 * i + a];
+        h[a] = (float)v;
+        l[a] = (float)(v - (double)h[a]);
+    }
+    hi[i] = make_float4(h[0], h[1], h[2], 0.f);
+    lo[i] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+// One component of x_j - x_i + n L (n in {-1, 0, 1}) from the FP32 pairs, in
+// FP32 only: the difference of the high parts and the addition of the high
+// part of n L are exact by Knuth's two-sum (s + e = a + b), the low parts and
+// the errors are then summed, and the result is rounded once.
+__device__ __forceinline__ float image_diff_pair(float hj, float lj, float hi, float li, int n,
+                                                 float Lh, float Ll) {
+    float s = __fsub_rn(hj, hi);
+    float bb = __fsub_rn(s, hj);
+    float err = __fadd_rn(__fsub_rn(hj, __fsub_rn(s, bb)), __fsub_rn(-hi, bb));
+    float low = __fsub_rn(lj, li);
+    if (n != 0) {
+        const float b = n > 0 ? Lh : -Lh;
+        const float s2 = __fadd_rn(s, b);
+        const float bb2 = __fsub_rn(s2, s);
+        err = __fadd_rn(err, __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bb2)), __fsub_rn(b, bb2)));
+        low = __fadd_rn(low, n > 0 ? Ll : -Ll);
+        s = s2;
+    }
+    return __fadd_rn(s, __fadd_rn(err, low));
+}
+
+// Warp per row: (u, r) of each of the row's edges, in CSR order.  The edge
+// vector is formed in FP32 from the positions' FP32 pairs (FP64 runs at a
+// small fraction of the FP32 rate on this GPU); it agrees with the FP64
+// formula of edge_vector to within one FP32 rounding.
 __global__ void k_edge_geometry(int64_t n, const int64_t* __restrict__ row_ptr,
                                 const int32_t* __restrict__ col, const int8_t* __restrict__ shift,
-                                const double* __restrict__ x, EdgeConst k,
+                                const float4* __restrict__ hi, const float4* __restrict__ lo,
+                                float Lh0, float Lh1, float Lh2, float Ll0, float Ll1, float Ll2,
                                 float4* __restrict__ geo) {
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
+    const float4 hi_i = hi[i], lo_i = lo[i];
     for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
+        const int j = col[e];
+        const int code = shift[e];
+        const float4 hj = hi[j], lj = lo[j];
         float d[3], u[3];
-        edge_vector(x, i, col[e], shift[e], k, d);
+        d[0] = image_diff_pair(hj.x, lj.x, hi_i.x, lo_i.x, code / 9 - 1, Lh0, Ll0);
+        d[1] = image_diff_pair(hj.y, lj.y, hi_i.y, lo_i.y, (code / 3) % 3 - 1, Lh1, Ll1);
+        d[2] = image_diff_pair(hj.z, lj.z, hi_i.z, lo_i.z, code % 3 - 1, Lh2, Ll2);
         const float r = edge_unit(d, u);
         geo[e] = make_float4(u[0], u[1], u[2], r);
     }
@@ -997,11 +1046,20 @@ __global__ void k_edge_geometry(int64_t n, const int64_t* __restrict__ row_ptr,
 
 int launch_edge_geometry(int64_t n, const int64_t* row_ptr, const int32_t* col,
                          const int8_t* shift, const double* x, const EdgeConst& k, float4* geo,
-                         cudaStream_t st) {
+                         float4* split, cudaStream_t st) {
     if (n <= 0) return MP_OK;
+    float4* hi = split;
+    float4* lo = split + n;
+    k_split_positions<<<grid_for(n, 256), 256, 0, st>>>(n, x, hi, lo);
+    note_launch();
+    float Lh[3], Ll[3];
+    for (int a = 0; a < 3; ++a) {
+        Lh[a] = (float)k.L[a];
+        Ll[a] = (float)(k.L[a] - (double)Lh[a]);
+    }
     const int wpb = 8;
-    k_edge_geometry<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, st>>>(n, row_ptr, col, shift,
-                                                                           x, k, geo);
+    k_edge_geometry<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, 0, st>>>(
+        n, row_ptr, col, shift, hi, lo, Lh[0], Lh[1], Lh[2], Ll[0], Ll[1], Ll[2], geo);
     note_launch();
     MP_CUDA_TRY(cudaGetLastError());
     return MP_OK;

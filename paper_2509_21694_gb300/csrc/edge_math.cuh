@@ -1,6 +1,8 @@
 // Per-edge geometry and angular/radial features shared by the edge kernels.
 //
-//   d = fl64(fl64(x_j - x_i) + n L) rounded to FP32, r = |d|, u = d / r
+//   d = fl64(fl64(x_j - x_i) + n L) rounded to FP32 (the tensor-core path forms
+//   it from FP32 position pairs instead, within one FP32 rounding of this),
+//   r = |d|, u = d / r
 //   e_k(r) = sqrt(2 / r_c) sin(k pi r / r_c) / r,  k = 1..8
 //   u_env(x) = 1 - (p+1)(p+2)/2 x^p + p(p+2) x^(p+1) - p(p+1)/2 x^(p+2)
 //   eps_k = e_k u_env,  and d eps_k / d r for the adjoint

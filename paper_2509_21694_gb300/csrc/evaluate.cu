@@ -292,6 +292,7 @@ struct EvalBufs {
     double* vsum;     // [9] one sub-system's virial
     double* vtot;     // [9] all sub-systems', in sub-system order
     float4* geo;      // BF16: per edge (u, r) of the current sub-system
+    float4* split;    // BF16: the sub-system's positions as FP32 pairs (2 n)
 };
 
 // Rows a pass must cover: atoms within `hops` hops of a root (a prefix of
@@ -350,7 +351,7 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
     if (precision == MP_BF16) {   // edge geometry once for all of this sub-system's passes
         ea.geo = b.geo;
         TimerScope ts(ctx, MP_TIMER_PARTITION, ss.n_edges, n);
-        MP_TRY(launch_edge_geometry(n, ss.row_ptr, ss.col, ss.shift, x, kc, b.geo, st));
+        MP_TRY(launch_edge_geometry(n, ss.row_ptr, ss.col, ss.shift, x, kc, b.geo, b.split, st));
     }
     NodeArgs na{};
     na.inv_navg = kc.inv_navg;
@@ -554,10 +555,11 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
     b.floc = ws.floc.as<double>();
     b.eloc = ws.eatom.as<double>();
     b.vloc = b.vsum = b.vtot = nullptr;
-    b.geo = nullptr;
+    b.geo = b.split = nullptr;
     if (precision == MP_BF16) {
-        MP_TRY(ws.geo.reserve(sizeof(float4) * (emax + 1)));
+        MP_TRY(ws.geo.reserve(sizeof(float4) * (emax + 1 + 2 * nmax)));
         b.geo = ws.geo.as<float4>();
+        b.split = b.geo + emax + 1;
     }
     if (d_stress) {
         MP_TRY(ws.vir.reserve(sizeof(double) * (9 * nmax + 18)));

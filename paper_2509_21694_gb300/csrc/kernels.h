@@ -14,7 +14,7 @@ struct EdgeArgs {
     const int8_t* shift;
     const double* x;          // [n][3] wrapped positions
     // tensor-core kernels: per edge of this CSR, (u_x, u_y, u_z, r) of
-    // d = x_j - x_i + n L as edge_vector and edge_unit give it (launch_edge_geometry)
+    // d = x_j - x_i + n L (launch_edge_geometry)
     const float4* geo;
     EdgeConst k;
     const LayerW* w;
@@ -39,11 +39,12 @@ struct EdgeArgs {
 };
 
 // (u_x, u_y, u_z, r) of every edge of a CSR over n rows, for the tensor-core
-// edge kernels: the FP64 edge vector is formed once per evaluation instead
-// of once per edge kernel.
+// edge kernels, formed once per evaluation: the positions x [n][3] are split
+// into FP32 pairs (scratch `split`, 2 n float4) and each edge vector is
+// formed from them in FP32 arithmetic.
 int launch_edge_geometry(int64_t n, const int64_t* row_ptr, const int32_t* col,
                          const int8_t* shift, const double* x, const EdgeConst& k, float4* geo,
-                         cudaStream_t st);
+                         float4* split, cudaStream_t st);
 int launch_edge_fwd_f32(const Model& m, const EdgeArgs& a, cudaStream_t st);
 int launch_edge_bwd_f32(const Model& m, const EdgeArgs& a, cudaStream_t st);
 int launch_edge_fwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int num_sms);
