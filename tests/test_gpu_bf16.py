@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 import torch
 
+import gates
 import synth
 from oracle import model as om
 from oracle import neighbors as onb
@@ -87,9 +88,16 @@ def test_bf16_partitioned_equals_unpartitioned(mp, P, mode):
     w = synth.make_weights(d, 1)
     a = _run(mp, d, w, s, 2, mp.MP_BF16)
     b = _run(mp, d, w, s, 2, mp.MP_BF16, n_parts=P, halo_mode=mode)
-    frms = np.sqrt((a[1] ** 2).mean())
-    assert np.abs(a[1] - b[1]).max() <= 1e-6 * frms, np.abs(a[1] - b[1]).max() / frms
+    ok, gap = gates.output_gap(b[1], a[1])
+    assert ok, gap
     assert np.array_equal(a[2], b[2])
+    pot = mp.Potential(d, w)
+    pos = torch.tensor(s.pos, device="cuda")
+    sp = torch.tensor(s.species, device="cuda")
+    f64 = [gates.fp64_forces(mp, pot, pos, sp, s.box, 2, mp.MP_BF16, n_parts=q, halo_mode=mode)
+           for q in (1, P)]
+    pot.close()
+    assert gates.fp64_gap(f64[1], f64[0]) <= gates.GATE, gates.fp64_gap(f64[1], f64[0])
 
 
 def test_bf16_deterministic(mp):

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 import torch
 
+import gates
 import synth
 from oracle import partition as op
 
@@ -59,6 +60,12 @@ def test_262k_partitioned_equals_unpartitioned(mp, precision):
     p = mp.MP_FP32 if precision == "fp32" else mp.MP_BF16
     F1, E1 = _gpu(mp, s, d, w, p, 1)
     F8, E8 = _gpu(mp, s, d, w, p, 8)
-    frms = np.sqrt((F1 ** 2).mean())
-    assert np.abs(F8 - F1).max() <= 1e-6 * frms, np.abs(F8 - F1).max() / frms
+    ok, gap = gates.output_gap(F8, F1)
+    assert ok, gap
     assert np.array_equal(E1, E8)
+    pot = mp.Potential(d, w)
+    pos = torch.tensor(s.pos, device="cuda")
+    sp = torch.tensor(s.species, device="cuda")
+    f64 = [gates.fp64_forces(mp, pot, pos, sp, s.box, 2, p, n_parts=q) for q in (1, 8)]
+    pot.close()
+    assert gates.fp64_gap(f64[1], f64[0]) <= gates.GATE, gates.fp64_gap(f64[1], f64[0])

@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 import torch
 
+import gates
 import synth
 from oracle import model as om
 from oracle import neighbors as onb
@@ -207,8 +208,11 @@ def test_partitioned_evaluation_with_graph_parts_is_exact(mp, precision):
                                    n_parts=4, part=part)
     F0 = F0.cpu().numpy().astype(np.float64)
     F1 = F1.cpu().numpy().astype(np.float64)
-    frms = np.sqrt((F0 ** 2).mean())
-    assert np.abs(F1 - F0).max() <= 1e-6 * frms, np.abs(F1 - F0).max() / frms
+    ok, gap = gates.output_gap(F1, F0)
+    assert ok, gap
+    f64 = [gates.fp64_forces(mp, pot, pos, sp, s.box, 2, prec),
+           gates.fp64_forces(mp, pot, pos, sp, s.box, 2, prec, n_parts=4, part=part)]
+    assert gates.fp64_gap(f64[1], f64[0]) <= gates.GATE, gates.fp64_gap(f64[1], f64[0])
     assert np.array_equal(e0.cpu().numpy(), e1.cpu().numpy())
     assert abs(E1.item() - E0.item()) <= 1e-9 * abs(E0.item())
     if precision == "fp32":

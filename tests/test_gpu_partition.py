@@ -1,9 +1,12 @@
 """GPU partitions: plan sets against the oracle (bit-exact), partitioned E/F
-against unpartitioned (<= 1e-6 F_rms) and against the oracle."""
+against unpartitioned (the partition gate of tests/gates.py: FP64 force sums
+within 1e-6 F_rms, FP32 outputs within that plus one output rounding) and
+against the oracle."""
 import numpy as np
 import pytest
 import torch
 
+import gates
 import synth
 from oracle import model as om
 from oracle import neighbors as onb
@@ -61,8 +64,11 @@ def test_partitioned_equals_unpartitioned(mp, P, mode):
     E1, F1, e1 = pot.energy_forces(pos, sp, s.box, 2, n_parts=P, halo_mode=mode, per_atom=True)
     F0 = F0.cpu().numpy().astype(np.float64)
     F1 = F1.cpu().numpy().astype(np.float64)
-    frms = np.sqrt((F0 ** 2).mean())
-    assert np.abs(F1 - F0).max() <= 1e-6 * frms, np.abs(F1 - F0).max() / frms
+    ok, gap = gates.output_gap(F1, F0)
+    assert ok, gap
+    f64 = [gates.fp64_forces(mp, pot, pos, sp, s.box, 2, mp.MP_FP32, n_parts=q, halo_mode=mode)
+           for q in (1, P)]
+    assert gates.fp64_gap(f64[1], f64[0]) <= gates.GATE, gates.fp64_gap(f64[1], f64[0])
     # root energies are computed from identical inputs in identical order
     assert np.array_equal(e0.cpu().numpy(), e1.cpu().numpy())
     assert abs(E1.item() - E0.item()) <= 1e-9 * abs(E0.item())
@@ -110,7 +116,10 @@ def test_slabs_without_roots(mp, precision):
     E1, F1, e1 = pot.energy_forces(pos, sp, s.box, 2, precision, n_parts=128, per_atom=True)
     F0 = F0.cpu().numpy().astype(np.float64)
     F1 = F1.cpu().numpy().astype(np.float64)
-    assert np.abs(F1 - F0).max() <= 1e-6 * np.sqrt((F0 ** 2).mean())
+    ok, gap = gates.output_gap(F1, F0)
+    assert ok, gap
+    f64 = [gates.fp64_forces(mp, pot, pos, sp, s.box, 2, precision, n_parts=q) for q in (1, 128)]
+    assert gates.fp64_gap(f64[1], f64[0]) <= gates.GATE, gates.fp64_gap(f64[1], f64[0])
     assert np.array_equal(e0.cpu().numpy(), e1.cpu().numpy())
     pot.close()
 
