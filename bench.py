@@ -79,7 +79,7 @@ def parse():
 # 131,072 atoms, scaled by the edges of a launch.  The figure belongs to the
 # kernel sources whose hash is stored beside it: once those sources change,
 # the line reports traffic null until the counters are taken again.
-TRAFFIC_BYTES_PER_EDGE_BF16 = {"bwd": (459.8, "cbfa76d07f37a530")}
+TRAFFIC_BYTES_PER_EDGE_BF16 = {"bwd": (462.7, "4562b05898f33363")}
 TRAFFIC_SOURCES = ("edge_bf16.cu", "edge_math.cuh", "tc.cuh", "kernels.h", "common.cuh")
 
 
@@ -272,17 +272,19 @@ class Clocks:
 #   adjoint, layer >= 1 (symmetric pair: both directions of the edge):
 #     Y-weighted sums of both sides' adjoints (sk_l, sj_l)           32
 #     sender gradient dE/dh_k of the reverse edge                     22
-#     dE/dR_q of both directions contracted with dR_q/dr              50
-#     dE/dY_lm = R_la (ak_lm hj0 -+ aj_lm hk0)                         28
-#     dY/du contraction (v) and the pair-gradient share t u + v / r   43
-#                                                            total   175
-#   adjoint, layer 0 (no l >= 1 inputs): P_lm 24, P.Y 16, dE/dY 8,
-#     dR contraction 8, dY/du and pair gradient 43             total    99
+#     dE/dR_q of both directions contracted with dR_q/dr              49
+#     dE/dY_lm = R_la (ak_lm hj0 -+ aj_lm hk0), with the harmonics'
+#       constant factors folded into R_la                             30
+#     dY/du contraction (v, 9 multiply-adds) and the pair-gradient
+#       share t u + v / r                                             37
+#                                                            total   170
+#   adjoint, layer 0 (no l >= 1 inputs): P_lm 24, P.Y 16, dE/dY 10,
+#     dR contraction 8, dY/du and pair gradient 37             total    95
 #   forward, layer >= 1: A0 2, l = 1: 13, l = 2: 21            total    36
 #   forward, layer 0:                                          total    20
 # plus the first radial layer (K = 8 -> H = 64, FP32) per edge: value and
 # r-tangent in the adjoint (2 x 8 x 64 multiply-adds), value in the forward.
-FP32_FLOPS_PER_CHANNEL = {("bwd", False): 175, ("bwd", True): 99,
+FP32_FLOPS_PER_CHANNEL = {("bwd", False): 170, ("bwd", True): 95,
                           ("fwd", False): 36, ("fwd", True): 20}
 
 

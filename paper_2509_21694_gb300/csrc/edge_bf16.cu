@@ -515,6 +515,18 @@ __global__ void __launch_bounds__(FwdCfg<FIRST>::NTH, 1)
 
 // ------------------------------------------------------------------ adjoint --
 
+// v = sum_lm gY_lm dY_lm/du (lmax = 2) with the harmonics' constant factors
+// already in the operand: g_lm = sqrt3 gY_lm for l = 1 and sqrt15 gY_lm for
+// l = 2 (entry 0 unused).  The gradient of Y_20 = sqrt5/2 (3 z^2 - 1) is
+// 3 sqrt5 z = sqrt15 (sqrt3 z), and sqrt3 z is Y_1z, passed as y1z.
+__device__ __forceinline__ void sph_grad_prescaled(const float u[3], float y1z, const float* g,
+                                                   float v[3]) {
+    v[0] = fmaf(g[4], u[1], fmaf(g[7], u[2], fmaf(g[8], u[0], g[1])));
+    v[1] = fmaf(g[4], u[0], fmaf(g[5], u[2], fmaf(-g[8], u[1], g[2])));
+    v[2] = fmaf(g[5], u[1], fmaf(g[7], u[0], fmaf(g[6], y1z, g[3])));
+}
+constexpr float kS3 = 1.7320508075688772f, kS15 = 3.872983346207417f;
+
 // Sum over the warp's lanes of values held as unevaluated FP32 pairs
 // hi + lo, without FP64 arithmetic (whose rate on this GPU is a small
 // fraction of FP32's).  Each butterfly step adds two pairs with Knuth's
@@ -815,18 +827,21 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                         if (FIRST) {
                             // layer 0 (no l >= 1 inputs): P_lm = hj0 ak_lm -+ hk0 aj_lm enters
                             // both the radial term (through P_l . Y_l) and dE/dY (R_la P_lm)
+                            // (gy carries the harmonics' factors sqrt3 / sqrt15, see
+                            // sph_grad_prescaled)
+                            const float r1 = kS3 * R[PP::sla(1)], r2 = kS15 * R[PP::sla(2)];
                             float s1 = 0.f, s2 = 0.f;
 #pragma unroll
                             for (int m = 0; m < 3; ++m) {
                                 const float P = fmaf(hj0, ak[1 + m], -hk0 * ajc[1 + m]);
                                 s1 = fmaf(P, Y[1 + m], s1);
-                                gy[1 + m] = R[PP::sla(1)] * P;
+                                gy[1 + m] = r1 * P;
                             }
 #pragma unroll
                             for (int m = 0; m < 5; ++m) {
                                 const float P = fmaf(hj0, ak[4 + m], hk0 * ajc[4 + m]);
                                 s2 = fmaf(P, Y[4 + m], s2);
-                                gy[4 + m] = R[PP::sla(2)] * P;
+                                gy[4 + m] = r2 * P;
                             }
                             gr = fmaf(ak[0], hj0, ajc[0] * hk0) * dR[0];
                             gr = fmaf(s1, dR[PP::sla(1)], gr);
@@ -845,10 +860,9 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                                 sk2 = fmaf(ak[4 + m], Y[4 + m], sk2);
                             }
                             {   // dE/dh_k as the sender of the reverse edge (i <- k)
-                                float g0 = R[0] * ajc[0];
-                                g0 = fmaf(-R[PP::sla(1)], sj1, g0);
-                                g0 = fmaf(R[PP::sla(2)], sj2, g0);
-                                gacc[0] += g0;
+                                gacc[0] = fmaf(R[0], ajc[0], gacc[0]);
+                                gacc[0] = fmaf(-R[PP::sla(1)], sj1, gacc[0]);
+                                gacc[0] = fmaf(R[PP::sla(2)], sj2, gacc[0]);
 #pragma unroll
                                 for (int m = 0; m < 3; ++m) gacc[1 + m] = fmaf(R[PP::slb(1)], ajc[1 + m], gacc[1 + m]);
 #pragma unroll
@@ -857,9 +871,10 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                             // this channel's share of dE_pair/dd: radial part along u (both
                             // directions' dE/dR contracted with dR/dr) and the angular part
                             // through dE/dY; the l = 1 term of the reverse edge changes sign
-                            gr = fmaf(ak[0], hj0, ajc[0] * hk0) * dR[0];
-                            gr = fmaf(fmaf(hj0, sk1, -hk0 * sj1), dR[PP::sla(1)], gr);
-                            gr = fmaf(fmaf(hj0, sk2, hk0 * sj2), dR[PP::sla(2)], gr);
+                            // (grouped by the receiver's and the sender's h0)
+                            gr = hj0 * fmaf(ak[0], dR[0], fmaf(sk1, dR[PP::sla(1)], sk2 * dR[PP::sla(2)]));
+                            gr = fmaf(hk0, fmaf(ajc[0], dR[0], fmaf(-sj1, dR[PP::sla(1)], sj2 * dR[PP::sla(2)])),
+                                      gr);
                             {
                                 float g1b = 0.f, g2b = 0.f;
 #pragma unroll
@@ -871,9 +886,10 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                                 gr = fmaf(g1b, dR[PP::slb(1)], gr);
                                 gr = fmaf(g2b, dR[PP::slb(2)], gr);
                             }
-                            {
-                                const float a1 = R[PP::sla(1)] * hj0, b1 = R[PP::sla(1)] * hk0;
-                                const float a2 = R[PP::sla(2)] * hj0, b2 = R[PP::sla(2)] * hk0;
+                            {   // (with the harmonics' factors, see sph_grad_prescaled)
+                                const float r1 = kS3 * R[PP::sla(1)], r2 = kS15 * R[PP::sla(2)];
+                                const float a1 = r1 * hj0, b1 = r1 * hk0;
+                                const float a2 = r2 * hj0, b2 = r2 * hk0;
 #pragma unroll
                                 for (int m = 0; m < 3; ++m) gy[1 + m] = fmaf(ak[1 + m], a1, -ajc[1 + m] * b1);
 #pragma unroll
@@ -884,7 +900,7 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                         const float u[3] = {ue.x, ue.y, ue.z};
                         const float ir = ue.w;
                         float v[3];
-                        sph_grad<TLMAX, float>(u, gy, v);
+                        sph_grad_prescaled(u, Y[3], gy, v);
                         const float vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
                         if (STRESS) {
                             // the force share is accumulated exactly as without the
