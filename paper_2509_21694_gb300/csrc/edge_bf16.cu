@@ -34,11 +34,12 @@
 //      F_k = sum_e sum_c g_c(e).
 // The adjoint of a layer first compacts each row group's edges, in order,
 // without those between two atoms of the layer's outermost hop class (their
-// terms are exact zeros).  The epilogues gather the next edge's sender
-// features while the current one computes (layer 0 of the forward, which
-// gathers one value per edge, requests a whole slice's at once), and read
-// the radial outputs from tensor memory four edges at a time (forward) or
-// per edge (adjoint).  The forward's first radial layer forms two hidden
+// terms are exact zeros).  The epilogues gather sender features ahead of
+// the edge being computed: the adjoint the next edge's, the later-layer
+// forward three edges ahead (a ring of four edges' features), the layer-0
+// forward, which gathers one value per edge, a whole slice's at once.  They
+// read the radial outputs from tensor memory four (layer-0 forward), two
+// (later-layer forward) or one (adjoint) edges at a time.  The forward's first radial layer forms two hidden
 // units per packed FP32x2 FMA.
 // The MLP's hidden activations use the hardware tanh for the sigmoid: they
 // are rounded to BF16 for the next contraction anyway.
@@ -59,13 +60,16 @@ constexpr int NTH = 128 * NWG;     // threads per CTA
 constexpr int WG_COLS = 128;       // tensor-memory columns per warpgroup (D1 and D2 share them)
 // Forward: its per-thread state is smaller, so more warpgroups hide more of
 // the gathers' latency: six for layer 0 (one gathered value per edge), five
-// for the later layers (96 registers); D1 (64 columns) and a slice's D2
-// (3 or 5 paths x 16 columns) share 80 or 96 columns per warpgroup.
+// for the later layers (96 registers, which also hold a ring of the next
+// three edges' sender features); D1 (64 columns) and a slice's D2 (3 or 5
+// paths x 16 columns) share 80 or 96 columns per warpgroup.
 template <bool FIRST>
 struct FwdCfg {
     static constexpr int NWG = FIRST ? 6 : 5;
     static constexpr int NTH = 128 * NWG;
     static constexpr int COLS = FIRST ? 80 : 96;
+    static constexpr int PD = FIRST ? 0 : 3;   // later layers: sender prefetch distance
+    static constexpr int RB = FIRST ? 4 : 2;   // edges per tensor-memory load of R
 };
 constexpr int TM_COLS = 512;       // allocated per CTA
 // Receiver rows per row group.  All warpgroups of the GPU work on
@@ -422,7 +426,10 @@ __global__ void __launch_bounds__(FwdCfg<FIRST>::NTH, 1)
             for (int sl = 0; sl < SCF / 16; ++sl) {
                 // prefetch the first edges' sender features before waiting for
                 // the slice's MMA (col is 0, a valid row, for slots past the end)
-                float hjc[TNLM], hjn[TNLM], hjm[TNLM];
+                // later layers: a ring of PD + 1 edges' features, edge i + PD
+                // requested while edge i computes (the ring index is static: the
+                // slice loop is unrolled)
+                float hr[FIRST ? 1 : Cfg::PD + 1][TNLM];
                 // layer 0 gathers one value per edge (h0 of the sender): all 16 of
                 // the slice are requested at once, so their latency overlaps
                 float hb[FIRST ? 16 : 1];
@@ -430,35 +437,43 @@ __global__ void __launch_bounds__(FwdCfg<FIRST>::NTH, 1)
 #pragma unroll
                     for (int i = 0; i < 16; ++i)
                         hb[i] = __ldg(Hin + ((int64_t)w.col[sl * 16 + i] * TNLM) * TF + c);
-                }
-                if (!FIRST) {
-                    const int e0 = sl * 16;
-                    const float* __restrict__ hp = Hin + ((int64_t)w.col[e0] * TNLM) * TF + c;
+                } else {
 #pragma unroll
-                    for (int q = 0; q < TNLM; ++q) hjc[q] = (FIRST && q > 0) ? 0.f : __ldg(hp + q * TF);
-                    const float* __restrict__ hq = Hin + ((int64_t)w.col[e0 + 1] * TNLM) * TF + c;
+                    for (int d = 0; d < Cfg::PD; ++d) {
+                        const float* __restrict__ hp =
+                            Hin + ((int64_t)w.col[sl * 16 + d] * TNLM) * TF + c;
 #pragma unroll
-                    for (int q = 0; q < TNLM; ++q) hjn[q] = (FIRST && q > 0) ? 0.f : __ldg(hq + q * TF);
+                        for (int q = 0; q < TNLM; ++q) hr[d][q] = __ldg(hp + q * TF);
+                    }
                 }
                 if (!wg_wait(w, phase, g)) { alive = false; break; }
-                float Rb[PP::NP][4];
+                constexpr int RB = Cfg::RB;
+                float Rb[PP::NP][RB];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int e = sl * 16 + i;
                     const int lr = w.row[e];
                     if (lr < 0) break;
-                    if ((i & 3) == 0) {   // radial outputs of 4 edges per path at once
+                    if ((i & (RB - 1)) == 0) {   // radial outputs of RB edges per path at once
 #pragma unroll
-                        for (int q = 0; q < PP::NP; ++q) tc::tmem_ld4(tl + 16 * q + i, Rb[q]);
+                        for (int q = 0; q < PP::NP; ++q) {
+                            if (RB == 4)
+                                tc::tmem_ld4(tl + 16 * q + i, Rb[q]);
+                            else
+                                tc::tmem_ld2(tl + 16 * q + i, Rb[q]);
+                        }
                     }
                     float R[PP::NP];
 #pragma unroll
-                    for (int q = 0; q < PP::NP; ++q) R[q] = Rb[q][i & 3];
-                    if (!FIRST && i + 2 < 16) {
-                        const float* __restrict__ hp = Hin + ((int64_t)w.col[e + 2] * TNLM) * TF + c;
+                    for (int q = 0; q < PP::NP; ++q) R[q] = Rb[q][i & (RB - 1)];
+                    if (!FIRST && i + Cfg::PD < 16) {
+                        const float* __restrict__ hp =
+                            Hin + ((int64_t)w.col[e + Cfg::PD] * TNLM) * TF + c;
 #pragma unroll
-                        for (int q = 0; q < TNLM; ++q) hjm[q] = __ldg(hp + q * TF);
+                        for (int q = 0; q < TNLM; ++q)
+                            hr[FIRST ? 0 : (i + Cfg::PD) % (Cfg::PD + 1)][q] = __ldg(hp + q * TF);
                     }
+                    const float* hjc = hr[FIRST ? 0 : i % (Cfg::PD + 1)];
                     if (lr != cur) {
                         if (cur >= 0) {
                             write_row(cur, false);
@@ -484,11 +499,6 @@ __global__ void __launch_bounds__(FwdCfg<FIRST>::NTH, 1)
                     for (int m = 0; m < 5; ++m) {
                         acc[4 + m] = fmaf(t2, w.Y[e][3 + m], acc[4 + m]);
                         if (!FIRST) acc[4 + m] = fmaf(R[PP::slb(2)], hjc[4 + m], acc[4 + m]);
-                    }
-#pragma unroll
-                    for (int q = 0; q < TNLM; ++q) {
-                        hjc[q] = hjn[q];
-                        hjn[q] = hjm[q];
                     }
                 }
                 tc::fence_before_sync();
