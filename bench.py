@@ -79,7 +79,7 @@ def parse():
 # 131,072 atoms, scaled by the edges of a launch.  The figure belongs to the
 # kernel sources whose hash is stored beside it: once those sources change,
 # the line reports traffic null until the counters are taken again.
-TRAFFIC_BYTES_PER_EDGE_BF16 = {"bwd": (459.8, "645bee1565d70a84")}
+TRAFFIC_BYTES_PER_EDGE_BF16 = {"bwd": (462.8, "97d20bf04ec8b4bc")}
 TRAFFIC_SOURCES = ("edge_bf16.cu", "edge_math.cuh", "tc.cuh", "kernels.h", "common.cuh")
 
 
@@ -282,25 +282,24 @@ class Clocks:
 #     dR contraction 8, dY/du and pair gradient 37             total    95
 #   forward, layer >= 1: A0 2, l = 1: 13, l = 2: 21            total    36
 #   forward, layer 0:                                          total    20
-# plus the first radial layer (K = 8 -> H = 64, FP32) per edge: value and
-# r-tangent in the adjoint (2 x 8 x 64 multiply-adds), value in the forward.
+# (all three radial-MLP layers run on the tensor cores; the first, K = 8,
+# as one zero-padded K = 16 MMA, counted at its algorithmic K = 8).
 FP32_FLOPS_PER_CHANNEL = {("bwd", False): 170, ("bwd", True): 95,
                           ("fwd", False): 36, ("fwd", True): 20}
 
 
 def edge_fp32_flops(kind: str, F: int, first: bool) -> float:
-    H, NB = 64, 8
-    rows = 2 if kind == "bwd" else 1
-    return float(FP32_FLOPS_PER_CHANNEL[(kind, first)] * F + rows * 2 * NB * H)
+    return float(FP32_FLOPS_PER_CHANNEL[(kind, first)] * F)
 
 
 def edge_tensor_flops(kind: str, F: int, lmax: int, first: bool) -> float:
-    """BF16 tensor-core FLOPs per edge: radial-MLP layers 2 and 3 (H x H and
-    H x paths F), for the value row and, in the adjoint, its r-tangent row."""
-    H = 64
+    """BF16 tensor-core FLOPs per edge: the three radial-MLP layers (NB x H,
+    H x H and H x paths F), for the value row and, in the adjoint, its
+    r-tangent row."""
+    H, NB = 64, 8
     n_paths = (1 + lmax) if first else (1 + 2 * lmax)
     rows = 2 if kind == "bwd" else 1
-    return 2.0 * rows * (H * H + H * n_paths * F)
+    return 2.0 * rows * (NB * H + H * H + H * n_paths * F)
 
 
 def load_peaks():

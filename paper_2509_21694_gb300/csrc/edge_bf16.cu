@@ -1,30 +1,32 @@
-// Edge kernels with the radial MLP's dense contractions on tcgen05 tensor
+// Edge kernels with the radial MLP's three contractions on tcgen05 tensor
 // cores (BF16 operands, FP32 accumulation in tensor memory).  Geometry, the
-// first radial layer (K = 8), messages, adjoint sums and forces stay FP32 on
-// CUDA cores.  Shapes compiled: F = 128, lmax = 2, H = 64.
+// radial basis, messages, adjoint sums and forces stay FP32 on CUDA cores.
+// Shapes compiled: F = 128, lmax = 2, H = 64.
 //
-// A CTA holds one copy of the W2 / W3 operand tiles and runs independent
-// warpgroups (six or five in the forward, four in the adjoint, whose
-// per-thread state needs more registers); each warpgroup owns a stream of
-// receiver-row groups, its tensor-memory columns (80 / 96 forward, 128 adjoint),
-// an mbarrier and a named barrier, so one warpgroup's MMAs overlap the
-// others' CUDA-core work.  The geometry (unit vector and r of every edge) is
-// formed once per sub-system by k_edge_geometry and read here.
+// A CTA holds one copy of the W1 / W2 / W3 operand tiles and runs
+// independent warpgroups (six or five in the forward, four or five in the
+// adjoint, whose per-thread state needs more registers); each warpgroup owns
+// a stream of receiver-row groups, its tensor-memory columns (80 / 96
+// forward, 96 / 128 adjoint), an mbarrier and a named barrier, so one
+// warpgroup's MMAs overlap the others' CUDA-core work.  The geometry (unit
+// vector and r of every edge) is formed once per sub-system by
+// k_edge_geometry and read here.
 //
 // Per super-chunk of edges of the warpgroup's rows (128 edges forward; 64
 // edges plus their r-tangents in the adjoint):
 //   1. thread = edge: geometry, eps (and d eps/dr), spherical harmonics;
-//      thread = tile row: a1 = silu(W1 eps) (adjoint rows also carry the
-//      tangent silu'(z1) W1 d eps/dr) -> BF16 K-major tile B (128 x 64).
-//   2. MMA1: D1[128 x 64] = B . W2^T   (lane = tile row, column = hidden).
-//   3. thread = tile row reads its D1 row: a2 = silu(z2) (tangent rows:
-//      silu'(z2) dz2, with silu'(z2) taken from the value row's lane) ->
-//      the same tile B, rewritten in place.
+//      the basis rows (adjoint: eps and d eps/dr of each edge in adjacent
+//      rows) -> BF16 K-major tile B as two-term splits (K = 32, see
+//      st_basis_row; the first layer to about 16 significant bits).
+//   2. MMA0: D0[128 x 64] = B . W1^T (two K = 16 instructions); thread =
+//      tile row reads its row: a1 = silu(z1) (tangent rows: silu'(z1) dz1,
+//      with z1 taken from the value row's lane) -> tile B (128 x 64).
+//   3. MMA1: D1[128 x 64] = B . W2^T; a2 = silu(z2) (tangent rows:
+//      silu'(z2) dz2) -> the same tile B, rewritten in place.
 //   4. per 16-row slice of B: MMA2 D2_q[128 x 16] = W3_q . slice^T for each
 //      radial path q (lane = channel, column = edge: R, and dR/dr in the
-//      adjoint, where rows / columns alternate edge and tangent); D2 reuses
-//      D1's tensor-memory columns.  The epilogue reads one edge's columns at
-//      a time and prefetches the next edge's sender features.
+//      adjoint, where rows / columns alternate edge and tangent).  D0, D1
+//      and D2 share the warpgroup's tensor-memory columns.
 //   5. thread = channel runs the message (forward) or symmetric-pair adjoint
 //      (backward) epilogue on the slice.  In the adjoint each channel forms
 //      its own share of dE_pair/dd and accumulates it over the receiver row
@@ -39,8 +41,7 @@
 // forward three edges ahead (a ring of four edges' features), the layer-0
 // forward, which gathers one value per edge, a whole slice's at once.  They
 // read the radial outputs from tensor memory four (layer-0 forward), two
-// (later-layer forward) or one (adjoint) edges at a time.  The forward's first radial layer forms two hidden
-// units per packed FP32x2 FMA.
+// (later-layer forward) or one (adjoint) edges at a time.
 // The MLP's hidden activations use the hardware tanh for the sigmoid: they
 // are rounded to BF16 for the next contraction anyway.
 // One thread issues the MMAs; completion is signalled through an mbarrier
@@ -97,30 +98,8 @@ template <int NP>
 struct alignas(1024) Tiles {
     __nv_bfloat16 W3[NP][128 * 64];  // NP x 16 KB, one 128-row tile per radial path
     __nv_bfloat16 W2[64 * 64];       // W2 (out, in), K-major
-    float W1[kH * kNB + 4];          // hidden 32..63 start 4 floats later (bank offset)
-    float2 W1p[kH / 2][kNB];         // forward: rows 2p and 2p + 1 side by side
+    __nv_bfloat16 W1[64 * 64];       // [W1_hi | W1_hi | W1_lo | 0] (out, K), K-major
 };
-
-// Row h of W1 in shared memory.
-__device__ __forceinline__ int w1_row(int h) { return h * kNB + (h >= 32 ? 4 : 0); }
-
-// Packed FP32 pairs (two lanes of one register pair per instruction).
-__device__ __forceinline__ uint64_t f2_pack(float2 v) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
-    return r;
-}
-__device__ __forceinline__ float2 f2_unpack(uint64_t r) {
-    float2 v;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-    return v;
-}
-// {a.x b.x + c.x, a.y b.y + c.y}, each rounded once (fma.rn.f32x2)
-__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
 
 // Sigmoid from the hardware tanh (PTX tanh.approx.f32, relative error about
 // 2^-11): its absolute error, at most about 2.4e-4, stays below the BF16
@@ -132,9 +111,7 @@ __device__ __forceinline__ float sigmoid_fast(float z) {
 }
 
 struct alignas(1024) WgState {
-    __nv_bfloat16 B[128 * 64];       // a1 tile, then a2 tile, of the super-chunk
-    float eps[SCB][kNB];
-    float deps[SCB][kNB];
+    __nv_bfloat16 B[128 * 64];       // basis rows, then the a1 and a2 tiles, of the super-chunk
     float Y[SCB][TNLM - 1];          // Y_lm for lm = 1..8 (Y_00 = 1)
     float u[SCB][4];                 // unit vector, r
     int row[SCB], col[SCB];
@@ -244,6 +221,34 @@ __device__ __forceinline__ void mma_k64(uint32_t d, const __nv_bfloat16* A, cons
     for (int kk = 0; kk < 4; ++kk) tc::mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc, kk > 0 ? 1u : 0u);
 }
 
+// D[tmem, 128 x 64] = A(128 x 32, the first four K chunks of a tile) .
+// W1(64 x 32)^T: the first radial layer, K = 8 in two-term BF16 splits
+// (two K = 16 instructions).
+__device__ __forceinline__ void mma_k32(uint32_t d, const __nv_bfloat16* A, const __nv_bfloat16* B) {
+    const uint64_t ad = tc::desc_sw128(tc::smem_u32(A));
+    const uint64_t bd = tc::desc_sw128(tc::smem_u32(B));
+    constexpr uint32_t idesc = tc::idesc_bf16(128, 64);
+    tc::mma_bf16(d, ad, bd, idesc, 0u);
+    tc::mma_bf16(d, ad + 2, bd + 2, idesc, 1u);
+}
+
+// A radial basis row of the first layer's A operand: K chunks
+// [eps_hi | eps_lo | eps_hi | 0] of tile row `row` (eps = eps_hi + eps_lo,
+// eps_hi its BF16 rounding).
+__device__ __forceinline__ void st_basis_row(__nv_bfloat16* tile, int row, const float eps[kNB]) {
+    float hi[kNB], lo[kNB];
+#pragma unroll
+    for (int q = 0; q < kNB; ++q) {
+        hi[q] = __bfloat162float(__float2bfloat16_rn(eps[q]));
+        lo[q] = eps[q] - hi[q];
+    }
+    st_row_chunk(tile, row, 0, hi);
+    st_row_chunk(tile, row, 1, lo);
+    st_row_chunk(tile, row, 2, hi);
+    *reinterpret_cast<uint4*>(reinterpret_cast<unsigned char*>(tile) + row * 128 +
+                              (((3 ^ (row & 7)) & 7) << 4)) = make_uint4(0u, 0u, 0u, 0u);
+}
+
 // Bounded wait of one warpgroup on its mbarrier; uniform result.
 template <class W>
 __device__ __forceinline__ bool wg_wait(W& w, uint32_t& phase, int g) {
@@ -268,11 +273,22 @@ __device__ __forceinline__ void tc_setup(S& s, const LayerW& wl, int np, bool fi
         uint4* dst = reinterpret_cast<uint4*>(s.t.W3[p]);
         for (int q = tid; q < 128 * 64 * 2 / 16; q += NT) dst[q] = __ldg(&src[q]);
     }
-    for (int q = tid; q < kH * kNB; q += NT) {
-        const float v = __ldg(&wl.W1[q]);
-        s.t.W1[w1_row(q / kNB) + q % kNB] = v;
-        (q / kNB) & 1 ? (void)(s.t.W1p[q / kNB / 2][q % kNB].y = v)
-                      : (void)(s.t.W1p[q / kNB / 2][q % kNB].x = v);
+    // W1 (64 x 8, FP32) as a BF16 K-major 128-byte-swizzled tile of two-term
+    // splits W1 = W1_hi + W1_lo: K chunks [W1_hi | W1_hi | W1_lo | 0], against
+    // basis rows [eps_hi | eps_lo | eps_hi | 0] (the first radial layer's MMA
+    // reads K = 0..31), so that the product is W1_hi eps_hi + W1_hi eps_lo +
+    // W1_lo eps_hi: the first layer to about 16 significant bits
+    for (int q = tid; q < 64 * 64; q += NT) {
+        const int h = q >> 6, k = q & 63, part = k >> 3;
+        float v = 0.f;
+        if (part < 3) {
+            const float w1 = __ldg(&wl.W1[h * kNB + (k & 7)]);
+            const float hi = __bfloat162float(__float2bfloat16_rn(w1));
+            v = part < 2 ? hi : w1 - hi;
+        }
+        *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(s.t.W1) + h * 128 +
+                                          (((part ^ (h & 7)) & 7) << 4) + (k & 7) * 2) =
+            __float2bfloat16_rn(v);
     }
     if ((tid & 127) == 0) {
         tc::mbar_init(&s.wg[tid >> 7].mbar, 1);
@@ -366,7 +382,7 @@ __global__ void __launch_bounds__(FwdCfg<FIRST>::NTH, 1)
             for (int q = 0; q < TNLM; ++q) o[q * TF] = zero ? 0.f : acc[q] * a.k.inv_navg;
         };
         for (int64_t sc = e_beg; sc < e_end && alive; sc += SCF) {
-            {   // geometry and a1 of edge lt -> tile row lt
+            {   // geometry of edge lt; its radial basis -> tile row lt
                 float eps[kNB], deps[kNB], Y[TNLM], u4[4];
                 int col;
                 const int lr = edge_geometry<false>(a, w.rp, sc + lt, e_end, r0, nrows, eps, deps,
@@ -375,25 +391,26 @@ __global__ void __launch_bounds__(FwdCfg<FIRST>::NTH, 1)
                 w.col[lt] = col;
 #pragma unroll
                 for (int q = 1; q < TNLM; ++q) w.Y[lt][q - 1] = Y[q];
-                // two hidden units per packed FMA: {W1[h], W1[h+1]} x {eps, eps}
-                uint64_t ee[kNB];
+                st_basis_row(w.B, lt, eps);
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            wg_sync(g);
+            if (lt == 0) {   // MMA0: z1 = eps . W1^T
+                tc::fence_after_sync();
+                mma_k32(tb, w.B, s.t.W1);
+                tc::mma_commit(&w.mbar);
+            }
+            if (!wg_wait(w, phase, g)) { alive = false; break; }
 #pragma unroll
-                for (int b = 0; b < kNB; ++b) ee[b] = f2_pack(make_float2(eps[b], eps[b]));
-#pragma unroll 1
-                for (int j = 0; j < 8; ++j) {
-                    float v[8];
+            for (int h = 0; h < 4; ++h) {   // a1 = silu(z1): lane lt holds tile row lt
+                float z[16];
+                tc::tmem_ld16(tl + 16 * h, z);
+                tc::tmem_wait_ld();
 #pragma unroll
-                    for (int q = 0; q < 8; q += 2) {
-                        uint64_t acc = f2_pack(make_float2(0.f, 0.f));
-#pragma unroll
-                        for (int b = 0; b < kNB; ++b)
-                            acc = f2_fma(f2_pack(s.t.W1p[(8 * j + q) / 2][b]), ee[b], acc);
-                        const float2 z = f2_unpack(acc);
-                        v[q] = z.x * sigmoid_fast(z.x);
-                        v[q + 1] = z.y * sigmoid_fast(z.y);
-                    }
-                    st_row_chunk(w.B, lt, j, v);
-                }
+                for (int q = 0; q < 16; ++q) z[q] = z[q] * sigmoid_fast(z[q]);
+                st_row_chunk(w.B, lt, 2 * h, z);
+                st_row_chunk(w.B, lt, 2 * h + 1, z + 8);
             }
             tc::fence_proxy_async();
             tc::fence_before_sync();
@@ -684,50 +701,35 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                     w.row[lt] = lr;
                     w.col[lt] = col;
 #pragma unroll
-                    for (int q = 0; q < kNB; ++q) {
-                        w.eps[lt][q] = eps[q];
-                        w.deps[lt][q] = deps[q];
-                    }
-#pragma unroll
                     for (int q = 1; q < TNLM; ++q) w.Y[lt][q - 1] = Y[q];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) w.u[lt][q] = u4[q];
+                    // tile rows 2 e (the basis of edge e) and 2 e + 1 (its r-derivative)
+                    st_basis_row(w.B, 2 * lt, eps);
+                    st_basis_row(w.B, 2 * lt + 1, deps);
                 }
+                tc::fence_proxy_async();
+                tc::fence_before_sync();
                 wg_sync(g);
-                {   // tile rows 2 e (a1 of edge e) and 2 e + 1 (its r-tangent): each lane of
-                    // the pair forms z1 and dz1 for half of the hidden units, evaluates
-                    // both rows' activations there and swaps the half its partner needs
-                    const int e = lt >> 1, t = lt & 1;
-                    float src[kNB], dsrc[kNB];
+                if (lt == 0) {   // MMA0: z1 = eps . W1^T, dz1 = (d eps/dr) . W1^T
+                    tc::fence_after_sync();
+                    mma_k32(tb, w.B, s.t.W1);
+                    tc::mma_commit(&w.mbar);
+                }
+                if (!wg_wait(w, phase, g)) { alive = false; break; }
 #pragma unroll
-                    for (int b = 0; b < kNB; ++b) {
-                        src[b] = w.eps[e][b];
-                        dsrc[b] = w.deps[e][b];
+                for (int h = 0; h < 4; ++h) {   // value rows: silu(z1); tangent rows: silu'(z1) dz1
+                    float z[16];
+                    tc::tmem_ld16(tl + 16 * h, z);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float zv = __shfl_sync(0xffffffffu, z[q], lane & ~1);
+                        const float sg = sigmoid_fast(zv);
+                        z[q] = (lane & 1) ? sg * fmaf(zv, 1.f - sg, 1.f) * z[q] : zv * sg;
                     }
-#pragma unroll 1
-                    for (int j = 0; j < 4; ++j) {
-                        float keep[8], give[8];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const float* wr = s.t.W1 + w1_row(32 * t + 8 * j + q);
-                            float z = 0.f, dz = 0.f;
-#pragma unroll
-                            for (int b = 0; b < kNB; ++b) {
-                                z = fmaf(wr[b], src[b], z);
-                                dz = fmaf(wr[b], dsrc[b], dz);
-                            }
-                            const float sg = sigmoid_fast(z);
-                            const float val = z * sg;
-                            const float tan = sg * fmaf(z, 1.f - sg, 1.f) * dz;
-                            keep[q] = t ? tan : val;
-                            give[q] = t ? val : tan;
-                        }
-                        float got[8];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) got[q] = __shfl_xor_sync(0xffffffffu, give[q], 1);
-                        st_row_chunk(w.B, lt, 4 * t + j, keep);
-                        st_row_chunk(w.B, lt, 4 * (1 - t) + j, got);
-                    }
+                    st_row_chunk(w.B, lt, 2 * h, z);
+                    st_row_chunk(w.B, lt, 2 * h + 1, z + 8);
                 }
                 tc::fence_proxy_async();
                 tc::fence_before_sync();

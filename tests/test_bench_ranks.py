@@ -45,16 +45,16 @@ def test_single_rank_needs_no_process_group():
 
 
 def test_roofline_accounting():
-    """The per-edge work the roofline divides by: the tensor part is the two
-    BF16 radial layers (value row, plus the r-tangent row in the adjoint),
-    the FP32 part the per-channel epilogue plus the first radial layer; the
-    node kernels' bytes are each array read or written once."""
+    """The per-edge work the roofline divides by: the tensor part is the
+    three BF16 radial layers (value row, plus the r-tangent row in the
+    adjoint), the FP32 part the per-channel epilogue; the node kernels'
+    bytes are each array read or written once."""
     import bench
     F, H = 128, 64
-    assert bench.edge_tensor_flops("fwd", F, 2, False) == 2 * (H * H + H * 5 * F)
-    assert bench.edge_tensor_flops("bwd", F, 2, True) == 2 * 2 * (H * H + H * 3 * F)
-    assert bench.edge_fp32_flops("bwd", F, False) == 170 * F + 2 * 2 * 8 * H
-    assert bench.edge_fp32_flops("fwd", F, True) == 20 * F + 2 * 8 * H
+    assert bench.edge_tensor_flops("fwd", F, 2, False) == 2 * (8 * H + H * H + H * 5 * F)
+    assert bench.edge_tensor_flops("bwd", F, 2, True) == 2 * 2 * (8 * H + H * H + H * 3 * F)
+    assert bench.edge_fp32_flops("bwd", F, False) == 170 * F
+    assert bench.edge_fp32_flops("fwd", F, True) == 20 * F
     row, lm = 4 * F, 4 * F * 8
     # forward, layer 0 of two: read A (9 rows) and h0, write S and h' (9 rows)
     assert bench.node_bytes_per_atom("fwd", True, False) == (row + lm) + row + row + (row + lm)
