@@ -4,10 +4,10 @@
 // Shapes compiled: F = 128, lmax = 2, H = 64.
 //
 // A CTA holds one copy of the W1 / W2 / W3 operand tiles and runs
-// independent warpgroups (six or five in the forward, four or five in the
+// independent warpgroups (six or five in the forward, six or four in the
 // adjoint, whose per-thread state needs more registers); each warpgroup owns
 // a stream of receiver-row groups, its tensor-memory columns (80 / 96
-// forward, 96 / 128 adjoint), an mbarrier and a named barrier, so one
+// forward, 64 / 128 adjoint), an mbarrier and a named barrier, so one
 // warpgroup's MMAs overlap the others' CUDA-core work.  The geometry (unit
 // vector and r of every edge) is formed once per sub-system by
 // k_edge_geometry and read here.
@@ -110,6 +110,9 @@ __device__ __forceinline__ float sigmoid_fast(float z) {
     return fmaf(0.5f, t, 0.5f);
 }
 
+// The adjoint's warpgroup state; the virial partials exist with STRESS, the
+// per-thread compensated force sums with FKS.
+template <bool STRESS, bool FKS>
 struct alignas(1024) WgState {
     __nv_bfloat16 B[128 * 64];       // basis rows, then the a1 and a2 tiles, of the super-chunk
     float Y[SCB][TNLM - 1];          // Y_lm for lm = 1..8 (Y_00 = 1)
@@ -117,9 +120,10 @@ struct alignas(1024) WgState {
     int row[SCB], col[SCB];
     int klist[KWIN];                 // adjoint: kept edges of a window (offsets from its start)
     int kwarp[4];
-    float2 fpart[RPG][4][3];         // per-row, per-warp force partial sums (hi, lo)
-    float2 vpart[RPG][4][9];         // per-row, per-warp virial partial sums (stress)
-    int64_t rp[RPG + 1];
+    float2 fpart[RPG_B][4][3];       // per-row, per-warp force partial sums (hi, lo)
+    float2 vpart[RPG_B][4][STRESS ? 9 : 1];   // per-row, per-warp virial partial sums
+    float fkc[FKS ? 6 : 1][128];     // per thread: compensated row force sums (fk, fc)
+    int64_t rp[RPG_B + 1];
     int64_t next_grp;                // next row group, fetched by the leader
     uint64_t mbar;
     int abort;
@@ -139,13 +143,21 @@ struct alignas(1024) WgStateF {
 };
 
 // Adjoint: four warpgroups at up to 128 registers, except layer 0 without
-// the stress (no sender gradients, one gathered h value per edge), whose
-// state fits 96 registers and runs five.
+// the stress (no sender gradients, one gathered h value per edge), which
+// runs six at 80 registers: its compensated force sums live in shared
+// memory, seven of the nine sender alpha components are requested one edge
+// ahead and the other two when their edge starts, and its three radial
+// paths need 64 tensor-memory columns.
 template <bool FIRST, bool STRESS>
 struct BwdCfg {
-    static constexpr int NWG = (FIRST && !STRESS) ? 5 : 4;
+    static constexpr int NWG = (FIRST && !STRESS) ? 6 : 4;
     static constexpr int NTH = 128 * NWG;
-    static constexpr int COLS = (FIRST && !STRESS) ? 96 : 128;
+    static constexpr int COLS = (FIRST && !STRESS) ? 64 : 128;
+    // the compensated row force sums in shared memory instead of registers
+    static constexpr bool FKS = FIRST && !STRESS;
+    // sender alpha components requested one edge ahead (the rest are
+    // requested when their edge starts)
+    static constexpr int PFN = FKS ? 7 : 9;
 };
 
 template <int NP, class WG, int N>
@@ -155,7 +167,8 @@ struct SmemT {
     uint32_t taddr;
 };
 template <bool FIRST, bool STRESS>
-using SmemB = SmemT<FIRST ? 3 : 5, WgState, BwdCfg<FIRST, STRESS>::NWG>;   // adjoint
+using SmemB = SmemT<FIRST ? 3 : 5, WgState<STRESS, BwdCfg<FIRST, STRESS>::FKS>,
+                    BwdCfg<FIRST, STRESS>::NWG>;   // adjoint
 template <bool FIRST>
 using SmemF = SmemT<FIRST ? 3 : 5, WgStateF, FwdCfg<FIRST>::NWG>;          // forward
 template <class S>
@@ -586,7 +599,7 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
     auto& s = smem_as<SmemB<FIRST, STRESS>>(smem_raw);
     const int tid = threadIdx.x, g = tid >> 7, lt = tid & 127, warp = tid >> 5, lane = tid & 31;
     const int c = lt;
-    WgState& w = s.wg[g];
+    auto& w = s.wg[g];
     const float* __restrict__ Hin = a.Hin;
     const float* __restrict__ Alpha = a.Alpha;
     const float* __restrict__ Gout = a.Gout;
@@ -611,7 +624,12 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
         float gacc[TNLM], ak[TNLM], hk[TNLM];
         // this channel's share of the row force: FP32 partial sums over a slice
         // (fs), folded into a compensated row sum (fk, fc) once per slice
-        float fk[3] = {0.f, 0.f, 0.f}, fc[3] = {0.f, 0.f, 0.f}, fs[3] = {0.f, 0.f, 0.f};
+        float fk_r[3] = {0.f, 0.f, 0.f}, fc_r[3] = {0.f, 0.f, 0.f}, fs[3] = {0.f, 0.f, 0.f};
+        // (fk, fc) in registers, or in shared memory where registers bound the
+        // warpgroups per SM
+        float* __restrict__ fkc = &w.fkc[0][lt];
+        auto FK = [&](int q) -> float& { return Cfg::FKS ? fkc[q * 128] : fk_r[q]; };
+        auto FC = [&](int q) -> float& { return Cfg::FKS ? fkc[(3 + q) * 128] : fc_r[q]; };
         // with STRESS: this channel's share of the row's virial sum_e g_e (x) d_e
         // (a global sum, so plain FP32 per row suffices)
         float va[STRESS ? 9 : 1];
@@ -620,10 +638,11 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
         auto fold = [&]() {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                const float y = fs[q] - fc[q];
-                const float t = fk[q] + y;
-                fc[q] = (t - fk[q]) - y;
-                fk[q] = t;
+                const float fkq = FK(q), fcq = FC(q);
+                const float y = fs[q] - fcq;
+                const float t = fkq + y;
+                FC(q) = (t - fkq) - y;
+                FK(q) = t;
                 fs[q] = 0.f;
             }
         };
@@ -640,7 +659,7 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
             if (with_acc) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {   // this channel's share is fk - fc
-                    float hi = fk[q], lo = -fc[q];
+                    float hi = FK(q), lo = -FC(q);
                     warp_sum_pair(hi, lo);
                     if (lane == 0) w.fpart[lr][warp & 3][q] = make_float2(hi, lo);
                 }
@@ -772,7 +791,7 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                         const int64_t jb = ((int64_t)w.col[sl * 8] * TNLM) * TF + c;
 #pragma unroll
                         for (int q = 0; q < TNLM; ++q) {
-                            ajc[q] = __ldg(Alpha + jb + q * TF);
+                            if (q < Cfg::PFN) ajc[q] = __ldg(Alpha + jb + q * TF);
                             hjc[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + jb + q * TF);
                         }
                     }
@@ -785,6 +804,11 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                         const int e = sl * 8 + i;
                         const int lr = w.row[e];
                         if (lr < 0) return false;
+                        if (Cfg::PFN < TNLM) {   // this edge's components not requested ahead
+                            const int64_t jc = ((int64_t)w.col[e] * TNLM) * TF + c;
+#pragma unroll
+                            for (int q = Cfg::PFN; q < TNLM; ++q) ajc[q] = __ldg(Alpha + jc + q * TF);
+                        }
                         float R[PP::NP], dR[PP::NP];
 #pragma unroll
                         for (int q = 0; q < PP::NP; ++q) {
@@ -797,7 +821,7 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                             const int64_t jn = ((int64_t)w.col[e + 1] * TNLM) * TF + c;
 #pragma unroll
                             for (int q = 0; q < TNLM; ++q) {
-                                ajn[q] = __ldg(Alpha + jn + q * TF);
+                                if (q < Cfg::PFN) ajn[q] = __ldg(Alpha + jn + q * TF);
                                 hjn[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + jn + q * TF);
                             }
                         }
@@ -818,7 +842,7 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                                 hk[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + base + q * TF);
                             }
 #pragma unroll
-                            for (int q = 0; q < 3; ++q) fk[q] = fc[q] = 0.f;
+                            for (int q = 0; q < 3; ++q) FK(q) = FC(q) = 0.f;
                             if (STRESS) {
 #pragma unroll
                                 for (int q = 0; q < 9; ++q) va[q] = 0.f;
