@@ -46,53 +46,79 @@ __device__ __forceinline__ int local_class(const int32_t* cnt, int K, int64_t l)
 }
 
 // Local degree of every row, and per class m the number of local edges whose
-// two ends are both of class m (esame[m], accumulated).  Every lane of a warp
-// reaches the warp-wide reductions, also past the end of the rows.
-__global__ void k_local_deg(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                            const int32_t* __restrict__ gid, const int32_t* __restrict__ g2l,
-                            int64_t n, const int32_t* __restrict__ cnt, int K,
-                            int32_t* __restrict__ deg, unsigned long long* __restrict__ esame) {
-    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// two ends are both of class m (esame[m], accumulated).  A warp takes one
+// extended row at a time (grid-stride) and reads its global edges 32 at a
+// time, so the col and g2l loads of a step are one contiguous segment;
+// rows l >= n_ext get degree 0.  The same-class counts are summed per block
+// in shared memory (rows come class by class, so a block meets few classes)
+// and added to esame once per class and block.
+__global__ void __launch_bounds__(256) k_local_deg(
+    const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+    const int32_t* __restrict__ gid, const int32_t* __restrict__ g2l, int64_t n,
+    const int32_t* __restrict__ cnt, int K, int32_t* __restrict__ deg,
+    unsigned long long* __restrict__ esame) {
+    extern __shared__ unsigned long long s_same[];   // K + 1 counters
+    for (int m = threadIdx.x; m <= K; m += blockDim.x) s_same[m] = 0ull;
+    __syncthreads();
     const int64_t n_ext = ext_rows(cnt, K);
-    int m = K + 1, c = 0, same = 0;
-    if (l < n_ext) {
-        m = local_class(cnt, K, l);
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < n_ext;
+         l += nwarps) {
+        const int m = local_class(cnt, K, l);
         const int s = gid[l];
-        for (int64_t e = row_ptr[s]; e < row_ptr[s + 1]; ++e) {
+        const int64_t e1 = row_ptr[s + 1];
+        int c = 0, same = 0;
+        for (int64_t e = row_ptr[s] + lane; e < e1; e += 32) {
             const int t = g2l[col[e]];
             if (t >= 0) {
                 ++c;
                 same += local_class(cnt, K, t) == m;
             }
         }
+        c = __reduce_add_sync(0xffffffffu, (unsigned)c);
+        same = __reduce_add_sync(0xffffffffu, (unsigned)same);
+        if (lane == 0) {
+            deg[l] = c;
+            if (same) atomicAdd(&s_same[m], (unsigned long long)same);
+        }
     }
-    if (l < n) deg[l] = c;
-    const unsigned full = 0xffffffffu;
-    const bool uniform = __all_sync(full, m == __shfl_sync(full, m, 0));
-    if (uniform) {
-        const unsigned tot = __reduce_add_sync(full, (unsigned)same);
-        if ((threadIdx.x & 31) == 0 && tot && m <= K) atomicAdd(&esame[m], (unsigned long long)tot);
-    } else if (same && m <= K) {
-        atomicAdd(&esame[m], (unsigned long long)same);
-    }
+    for (int64_t l = n_ext + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+         l += (int64_t)gridDim.x * blockDim.x)
+        deg[l] = 0;
+    __syncthreads();
+    for (int m = threadIdx.x; m <= K; m += blockDim.x)
+        if (s_same[m]) atomicAdd(&esame[m], s_same[m]);
 }
 
-__global__ void k_local_fill(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                             const int8_t* __restrict__ shift, const int32_t* __restrict__ gid,
-                             const int32_t* __restrict__ g2l, int64_t n,
-                             const int32_t* __restrict__ cnt, int K,
-                             const int64_t* __restrict__ lrow, int32_t* __restrict__ lcol,
-                             int8_t* __restrict__ lshift) {
-    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= n || l >= ext_rows(cnt, K)) return;
-    int s = gid[l];
-    int64_t o = lrow[l];
-    for (int64_t e = row_ptr[s]; e < row_ptr[s + 1]; ++e) {
-        int t = g2l[col[e]];
-        if (t >= 0) {
-            lcol[o] = t;
-            lshift[o] = shift[e];
-            ++o;
+// The local CSR: each extended row keeps its global edges, in order, whose
+// sender is in the extended set (col mapped to the local index).  A warp per
+// row (grid-stride), 32 edges per step, compacted by a ballot.
+__global__ void __launch_bounds__(256) k_local_fill(
+    const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+    const int8_t* __restrict__ shift, const int32_t* __restrict__ gid,
+    const int32_t* __restrict__ g2l, const int32_t* __restrict__ cnt, int K,
+    const int64_t* __restrict__ lrow, int32_t* __restrict__ lcol, int8_t* __restrict__ lshift) {
+    const int64_t n_ext = ext_rows(cnt, K);
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < n_ext;
+         l += nwarps) {
+        const int s = gid[l];
+        const int64_t e0 = row_ptr[s], e1 = row_ptr[s + 1];
+        int64_t o = lrow[l];
+        for (int64_t eb = e0; eb < e1; eb += 32) {
+            const int64_t e = eb + lane;
+            int t = -1;
+            if (e < e1) t = g2l[col[e]];
+            const unsigned keep = __ballot_sync(0xffffffffu, t >= 0);
+            if (t >= 0) {
+                const int64_t q = o + __popc(keep & below);
+                lcol[q] = t;
+                lshift[q] = shift[e];
+            }
+            o += __popc(keep);
         }
     }
 }
@@ -104,8 +130,18 @@ __global__ void k_local_fill(const int64_t* __restrict__ row_ptr, const int32_t*
 // atom is closer than (m+1) r_c + s_m, so it has class <= m + 1 with a
 // margin of 1e-6 / K over rounding, and any atom h hops from a root has
 // class <= h.
+// The slab bounds and class thresholds of partition p, formed on the host
+// with the same FP64 operations the definition above gives (lo = L p / P,
+// hi = L (p + 1) / P, thr[m - 1] = m r_c + s_m), so that each atom costs one
+// division (its root bin) instead of one per threshold.
+constexpr int kGeomThr = 16;
+struct ClassGeom {
+    double lo, hi;
+    double thr[kGeomThr];   // m = 1..min(K, kGeomThr); larger m formed in the kernel
+};
+
 __global__ void k_class_geom(const double* __restrict__ xs, int64_t n, double Lz, int P, int p,
-                             double rc, int K, int32_t* __restrict__ cls) {
+                             double rc, int K, ClassGeom cg, int32_t* __restrict__ cls) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const double z = xs[3 * s + 2];
@@ -113,16 +149,22 @@ __global__ void k_class_geom(const double* __restrict__ xs, int64_t n, double Lz
         cls[s] = 0;
         return;
     }
-    const double lo = __ddiv_rn(__dmul_rn(Lz, (double)p), (double)P);
-    const double hi = __ddiv_rn(__dmul_rn(Lz, (double)(p + 1)), (double)P);
+    const double lo = cg.lo, hi = cg.hi;
     const bool below = z < lo;
     const double d_lo = below ? __dsub_rn(lo, z) : __dsub_rn(__dadd_rn(lo, Lz), z);
     const double d_hi = below ? __dsub_rn(__dadd_rn(z, Lz), hi) : __dsub_rn(z, hi);
     const double dist = d_lo < d_hi ? d_lo : d_hi;
     int c = K + 1;
     for (int m = 1; m <= K; ++m) {
-        const double slack = m == K ? 1e-6 : __ddiv_rn(__dmul_rn(1e-6, (double)m), (double)K);
-        if (dist < __dadd_rn(__dmul_rn((double)m, rc), slack)) { c = m; break; }
+        double thr;
+        if (m <= kGeomThr) {
+            thr = cg.thr[m - 1];
+        } else {
+            const double slack =
+                m == K ? 1e-6 : __ddiv_rn(__dmul_rn(1e-6, (double)m), (double)K);
+            thr = __dadd_rn(__dmul_rn((double)m, rc), slack);
+        }
+        if (dist < thr) { c = m; break; }
     }
     cls[s] = c;
 }
@@ -345,7 +387,15 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
         int32_t* cnt = d_cnt + (size_t)p * (K + 1);
         int32_t* cur = cls;
         if (mode == MP_HALO_GEOM) {
-            k_class_geom<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, rc, K, cls);
+            ClassGeom cg;
+            cg.lo = Lz * (double)p / (double)n_parts;
+            cg.hi = Lz * (double)(p + 1) / (double)n_parts;
+            for (int m = 1; m <= K && m <= kGeomThr; ++m) {
+                const double slack = m == K ? 1e-6 : 1e-6 * (double)m / (double)K;
+                cg.thr[m - 1] = (double)m * rc + slack;
+            }
+            k_class_geom<<<grid_for(n, 256), 256, 0, st>>>(xs, n, Lz, n_parts, p, rc, K, cg,
+                                                           cls);
             note_launch();
         } else {
             if (d_assign)
@@ -380,14 +430,16 @@ int build_plan(mp_ctx* ctx, const Graph& g, int n_parts, int k_hops, int mode, P
                                                             P.is_root.as<uint8_t>(), g2l);
             note_launch();
         }
-        k_local_deg<<<grid_for(n, 256), 256, 0, st>>>(
+        // a warp per extended row, grid-stride (the row count is on the device)
+        const int row_blocks = 8 * (ctx->num_sms > 0 ? ctx->num_sms : 152);
+        k_local_deg<<<row_blocks, 256, sizeof(unsigned long long) * (K + 1), st>>>(
             g.row_ptr.as<int64_t>(), g.col.as<int32_t>(), P.gid.as<int32_t>(), g2l, n, cnt, K, flag,
             reinterpret_cast<unsigned long long*>(d_stats + (size_t)p * ns + 2 * (K + 1)));
         note_launch();
         MP_TRY(exclusive_scan_i64(flag, P.row_ptr.as<int64_t>(), n, ws.tmp, st));
-        k_local_fill<<<grid_for(n, 256), 256, 0, st>>>(
+        k_local_fill<<<row_blocks, 256, 0, st>>>(
             g.row_ptr.as<int64_t>(), g.col.as<int32_t>(), g.shift.as<int8_t>(),
-            P.gid.as<int32_t>(), g2l, n, cnt, K, P.row_ptr.as<int64_t>(), P.col.as<int32_t>(),
+            P.gid.as<int32_t>(), g2l, cnt, K, P.row_ptr.as<int64_t>(), P.col.as<int32_t>(),
             P.shift.as<int8_t>());
         note_launch();
         k_plan_stats<<<1, 32, 0, st>>>(cnt, K, P.row_ptr.as<int64_t>(), d_stats + (size_t)p * ns);
