@@ -96,6 +96,7 @@ struct TPaths {
 // inputs are zero, else 5).
 template <int NP>
 struct alignas(1024) Tiles {
+    static constexpr int NPATH = NP;
     __nv_bfloat16 W3[NP][128 * 64];  // NP x 16 KB, one 128-row tile per radial path
     __nv_bfloat16 W2[64 * 64];       // W2 (out, in), K-major
     __nv_bfloat16 W1[64 * 64];       // [W1_hi | W1_hi | W1_lo | 0] (out, K), K-major
@@ -280,11 +281,13 @@ __device__ __forceinline__ void tc_setup(S& s, const LayerW& wl, int np, bool fi
     const uint4* src2 = reinterpret_cast<const uint4*>(wl.W2sw);
     uint4* dst2 = reinterpret_cast<uint4*>(s.t.W2);
     for (int q = tid; q < 64 * 64 * 2 / 16; q += NT) dst2[q] = __ldg(&src2[q]);
-    for (int p = 0; p < np; ++p) {
-        const int blk = first ? (p == 0 ? 0 : 2 * p - 1) : p;
-        const uint4* src = reinterpret_cast<const uint4*>(wl.W3sw + (size_t)blk * 128 * 64);
-        uint4* dst = reinterpret_cast<uint4*>(s.t.W3[p]);
-        for (int q = tid; q < 128 * 64 * 2 / 16; q += NT) dst[q] = __ldg(&src[q]);
+    if constexpr (decltype(s.t)::NPATH > 0) {
+        for (int p = 0; p < np; ++p) {
+            const int blk = first ? (p == 0 ? 0 : 2 * p - 1) : p;
+            const uint4* src = reinterpret_cast<const uint4*>(wl.W3sw + (size_t)blk * 128 * 64);
+            uint4* dst = reinterpret_cast<uint4*>(s.t.W3[p]);
+            for (int q = tid; q < 128 * 64 * 2 / 16; q += NT) dst[q] = __ldg(&src[q]);
+        }
     }
     // W1 (64 x 8, FP32) as a BF16 K-major 128-byte-swizzled tile of two-term
     // splits W1 = W1_hi + W1_lo: K chunks [W1_hi | W1_hi | W1_lo | 0], against
@@ -1009,6 +1012,477 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
     tc_teardown(s, phase, err, tid);
 }
 
+// ------------------------------------------ layer-0 adjoint by hidden unit --
+//
+// At layer 0 the senders' features are species embeddings (h0_j = Emb[s_j],
+// no l >= 1 inputs), so every channel sum of the adjoint factors through the
+// radial MLP's last layer.  With R_q = W3_q a2 (W3_q the 128 x 64 block of
+// radial path q) and the tangent dR_q/dr = W3_q da2,
+//   sum_c R_q[c] Emb[s][c] alpha_k[c, lm] = sum_h a2[h] V_k[s][lm][h],
+//   V_k[s][lm][h] = sum_c W3_q(l)[c][h] Emb[s][c] alpha_k[c, lm]
+// (q(0) = R0, q(1) = R_1a, q(2) = R_2a), and the same with da2.  V is formed
+// once per atom by k_v_first (FP32 on the CUDA cores, from the BF16 weight
+// values the forward multiplies by), and the edge kernel's epilogue then runs
+// over the 64 hidden units of an edge instead of its 128 channels, with no
+// third MMA: for edge e = (k <- j), hidden unit h,
+//   D_0 = Vk_0 + Vj_0,  D_1m = Vk_1m - Vj_1m,  D_2m = Vk_2m + Vj_2m
+//   (Vk = V_k[s_j][.][h], Vj = V_j[s_k][.][h]: the edge's two directions,
+//   Y_lm(-u) = (-1)^l Y_lm(u)),
+//   dE/dr share = da2[h] (D_0 + sum_lm Y_lm D_lm),
+//   dE/dY_lm share = a2[h] D_lm,
+// and the pair-gradient share t u + v / r is formed and summed over the
+// receiver row exactly as in the channel-wise kernel, the hidden units
+// taking the place of the channels in the per-row sums.
+
+constexpr int VTA = 8;            // atoms per tile of k_v_first
+constexpr int VTH = 512;          // its threads: 16 hidden quads x 8 atoms x 4 (l, m) groups
+struct alignas(16) VSmem {
+    float W[3][128][kH];          // W3 blocks of paths R0, R1a, R2a (FP32 of the BF16 values) x Emb[s]
+    float X[TNLM][128][VTA + 1];  // alpha of the tile's atoms, [lm][c][atom] (padded)
+};
+
+// V[a][s][lm][h] for atoms a < nrows (the rows with a nonzero adjoint).  The
+// CTA keeps the three weight blocks in shared memory and loops over tiles of
+// VTA atoms; a thread owns four hidden units of one atom and two or three
+// (l, m) rows: {0, 1, 2}, {3, 4}, {5, 6}, {7, 8}.
+__global__ void __launch_bounds__(VTH, 1)
+    k_v_first(int64_t nrows, const float* __restrict__ alpha, const float* __restrict__ emb,
+              int S, const __nv_bfloat16* __restrict__ W3b, float* __restrict__ V) {
+    extern __shared__ float4 vsm_raw[];
+    VSmem& s = *reinterpret_cast<VSmem*>(vsm_raw);
+    const int tid = threadIdx.x;
+    const int h4 = tid & 15, ta = (tid >> 4) & 7, grp = tid >> 7;
+    const int lm0 = grp == 0 ? 0 : 1 + 2 * grp;   // 0, 3, 5, 7
+    const int nlm = grp == 0 ? 3 : 2;
+    const int64_t ntiles = (nrows + VTA - 1) / VTA;
+    for (int sp = 0; sp < S; ++sp) {
+        __syncthreads();   // the previous species' weights consumed
+        // W3_q[c][h] Emb[s][c]: rounded alike in every partition, so the
+        // only partition-dependent roundings of V are those of its sum
+        for (int q = tid; q < 3 * 128 * kH; q += VTH) {
+            const int p = q / (128 * kH), r = q % (128 * kH);
+            const int blk = p == 0 ? 0 : 2 * p - 1;
+            (&s.W[0][0][0])[q] =
+                __bfloat162float(W3b[(size_t)blk * 128 * kH + r]) * __ldg(&emb[sp * 128 + r / kH]);
+        }
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int64_t a0 = tile * VTA;
+            __syncthreads();   // weights ready; the previous X consumed
+            for (int q = tid; q < VTA * TNLM * 128; q += VTH) {
+                const int a = q / (TNLM * 128), lm = (q / 128) % TNLM, c = q & 127;
+                const int64_t atom = a0 + a;
+                s.X[lm][c][a] = atom < nrows ? __ldg(&alpha[(atom * TNLM + lm) * 128 + c]) : 0.f;
+            }
+            __syncthreads();
+            // the channel sum in blocks of 16 (FP32 multiply-adds), the block
+            // sums added into an unevaluated pair hi + lo by two-sum: a per-
+            // partition adjoint's V stays within a few roundings of its exact
+            // value, so that partition sums of V agree with the whole system's
+            float hi[3][4], lo[3][4];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) hi[i][k] = lo[i][k] = 0.f;
+#pragma unroll 1
+            for (int cb = 0; cb < 128; cb += 16) {
+                float acc[3][4];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
+#pragma unroll 4
+                for (int c = cb; c < cb + 16; ++c) {
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        if (i < nlm) {
+                            const int lm = lm0 + i;
+                            const int path = lm == 0 ? 0 : (lm < 4 ? 1 : 2);
+                            const float4 wv = *reinterpret_cast<const float4*>(&s.W[path][c][4 * h4]);
+                            const float x = s.X[lm][c][ta];
+                            acc[i][0] = fmaf(x, wv.x, acc[i][0]);
+                            acc[i][1] = fmaf(x, wv.y, acc[i][1]);
+                            acc[i][2] = fmaf(x, wv.z, acc[i][2]);
+                            acc[i][3] = fmaf(x, wv.w, acc[i][3]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float sum = __fadd_rn(hi[i][k], acc[i][k]);
+                        const float bb = __fsub_rn(sum, hi[i][k]);
+                        const float err = __fadd_rn(__fsub_rn(hi[i][k], __fsub_rn(sum, bb)),
+                                                    __fsub_rn(acc[i][k], bb));
+                        hi[i][k] = sum;
+                        lo[i][k] = __fadd_rn(lo[i][k], err);
+                    }
+            }
+            float acc[3][4];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[i][k] = __fadd_rn(hi[i][k], lo[i][k]);
+            const int64_t atom = a0 + ta;
+            if (atom < nrows) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    if (i < nlm)
+                        *reinterpret_cast<float4*>(&V[((atom * S + sp) * TNLM + lm0 + i) * kH + 4 * h4]) =
+                            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            }
+        }
+    }
+}
+
+// The layer-0 hidden-unit adjoint: weight tiles W1 and W2 only.
+struct alignas(1024) Tiles0 {
+    static constexpr int NPATH = 0;
+    __nv_bfloat16 W2[64 * 64];
+    __nv_bfloat16 W1[64 * 64];
+};
+
+template <bool STRESS>
+struct alignas(1024) WgState0 {
+    __nv_bfloat16 B[128 * 64];       // basis rows, then the a1 and a2 tiles (row 2 e: edge e, 2 e + 1: its r-tangent)
+    float Y[SCB][TNLM - 1];          // Y_lm for lm = 1..8
+    float u[SCB][4];                 // unit vector, 1 / r
+    int row[SCB], col[SCB], sj[SCB];  // receiver row (-1: past the end), sender, sender species
+    int klist[KWIN];
+    int kwarp[4];
+    int spk[RPG_B];                  // species of the group's rows
+    float2 fpart[RPG_B][4][3];
+    float2 vpart[RPG_B][4][STRESS ? 9 : 1];
+    float fkc[6][128];               // per thread: compensated row force sums (fk, fc)
+    int64_t rp[RPG_B + 1];
+    int64_t next_grp;
+    uint64_t mbar;
+    int abort;
+};
+
+// Six warpgroups at 80 registers (the compensated row force sums in shared
+// memory), four with the stress (virial partials in registers).
+template <bool STRESS>
+struct Bwd0Cfg {
+    static constexpr int NWG = STRESS ? 4 : 6;
+    static constexpr int NTH = 128 * NWG;
+    static constexpr int COLS = 64;   // D0 and D1 (128 rows x 64 hidden units)
+    static constexpr bool FKS = !STRESS;
+};
+template <class WG, int N>
+struct SmemT0 {
+    Tiles0 t;
+    WG wg[N];
+    uint32_t taddr;
+};
+template <bool STRESS>
+using SmemB0 = SmemT0<WgState0<STRESS>, Bwd0Cfg<STRESS>::NWG>;
+static_assert(smem_fits<SmemB0<false>>() && smem_fits<SmemB0<true>>(),
+              "shared memory of the layer-0 hidden-unit adjoint");
+static_assert(Bwd0Cfg<false>::NWG * Bwd0Cfg<false>::COLS <= TM_COLS, "tensor memory");
+
+// Edges of a super-chunk: the warpgroup's first half (threads 0..63, one
+// hidden unit each) takes edges 0..31 in order, the second half edges 32..63,
+// each with its own receiver-row state; a row's force is the sum of the four
+// warps' shares (a warp's share of a row it did not meet stays zero).
+template <bool STRESS>
+__global__ void __launch_bounds__((Bwd0Cfg<STRESS>::NTH), 1)
+    k_edge_bwd0_tc(EdgeArgs a, LayerW wl, int64_t n_groups, int* err) {
+    using Cfg = Bwd0Cfg<STRESS>;
+    extern __shared__ unsigned char smem_raw[];
+    auto& s = smem_as<SmemB0<STRESS>>(smem_raw);
+    const int tid = threadIdx.x, g = tid >> 7, lt = tid & 127, warp = tid >> 5, lane = tid & 31;
+    const int half = lt >> 6, hu = lt & 63;   // edge half and hidden unit of this thread
+    auto& w = s.wg[g];
+    const float* __restrict__ Vf = a.vfirst;
+    const int S = a.n_species;
+    tc_setup<Cfg::NTH>(s, wl, 0, true, tid);
+    const uint32_t tb = s.taddr + Cfg::COLS * g;
+    const uint32_t tl = tb + ((uint32_t)(32 * (warp & 3)) << 16);
+    uint32_t phase = 0;
+    bool alive = true;
+    const unsigned char* Bb = reinterpret_cast<const unsigned char*>(w.B);
+
+    for (int64_t grp = (int64_t)blockIdx.x * Cfg::NWG + g; grp < n_groups && alive;
+         grp = next_group<Cfg::NWG>(w, a, g, lt)) {
+        const int64_t r0 = grp * RPG_B;
+        const int nrows = (int)min((int64_t)RPG_B, a.n - r0);
+        if (lt <= nrows) w.rp[lt] = a.row_ptr[r0 + lt];
+        if (lt < nrows) w.spk[lt] = a.species[r0 + lt];
+        for (int q = lt; q < RPG_B * 12; q += 128) (&w.fpart[0][0][0])[q] = make_float2(0.f, 0.f);
+        if (STRESS)
+            for (int q = lt; q < RPG_B * 36; q += 128)
+                (&w.vpart[0][0][0])[q] = make_float2(0.f, 0.f);
+        wg_sync(g);
+        const int64_t e_beg = w.rp[0], e_end = w.rp[nrows];
+        // this thread's share of the row force, each edge's share added into
+        // a compensated sum (fk, fc): a hidden unit's share of an edge is a
+        // sum over all channels, larger than a channel's share, so it is not
+        // first summed over several edges in plain FP32
+        float fk_r[3] = {0.f, 0.f, 0.f}, fc_r[3] = {0.f, 0.f, 0.f};
+        float* __restrict__ fkc = &w.fkc[0][lt];
+        auto FK = [&](int q) -> float& { return Cfg::FKS ? fkc[q * 128] : fk_r[q]; };
+        auto FC = [&](int q) -> float& { return Cfg::FKS ? fkc[(3 + q) * 128] : fc_r[q]; };
+        auto kadd = [&](int q, float gq) {
+            const float fkq = FK(q), fcq = FC(q);
+            const float y = gq - fcq;
+            const float t = fkq + y;
+            FC(q) = (t - fkq) - y;
+            FK(q) = t;
+        };
+        float va[STRESS ? 9 : 1];
+#pragma unroll
+        for (int q = 0; q < (STRESS ? 9 : 1); ++q) va[q] = 0.f;
+        auto flush = [&](int lr) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {   // this thread's share is fk - fc
+                float hi = FK(q), lo = -FC(q);
+                warp_sum_pair(hi, lo);
+                if (lane == 0) w.fpart[lr][warp & 3][q] = make_float2(hi, lo);
+            }
+            if (STRESS) {
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    float hi = va[q], lo = 0.f;
+                    warp_sum_pair(hi, lo);
+                    if (lane == 0) w.vpart[lr][warp & 3][q] = make_float2(hi, lo);
+                }
+            }
+        };
+        int cur = -1;
+        int sk = 0;                  // species of the current row
+        float vk[TNLM];              // V_k[s_j] of the current row (S = 1: loaded once per row)
+#pragma unroll
+        for (int q = 0; q < TNLM; ++q) vk[q] = 0.f;
+        const bool compact = a.n_recv > 0 && r0 + nrows > a.n_recv;
+        for (int64_t wb = e_beg; wb < e_end && alive;) {
+            const int64_t we = compact ? min(wb + (int64_t)KWIN, e_end) : e_end;
+            int64_t nk = we - wb;
+            if (compact) {
+                int keep[4], cnt = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t e = wb + 4 * lt + q;
+                    keep[q] = 0;
+                    if (e < we) {
+                        const int lr = find_row_t(w.rp, nrows, e);
+                        keep[q] = !(r0 + lr >= a.n_recv && (int64_t)a.col[e] >= a.n_recv);
+                    }
+                    cnt += keep[q];
+                }
+                int inc = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                if (lane == 31) w.kwarp[warp & 3] = inc;
+                wg_sync(g);
+                int off = inc - cnt;
+                for (int q = 0; q < (warp & 3); ++q) off += w.kwarp[q];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (keep[q]) w.klist[off++] = 4 * lt + q;
+                nk = w.kwarp[0] + w.kwarp[1] + w.kwarp[2] + w.kwarp[3];
+                wg_sync(g);
+            }
+            for (int64_t kc = 0; kc < nk && alive; kc += SCB) {
+                if (lt < SCB) {
+                    float eps[kNB], deps[kNB], Y[TNLM], u4[4];
+                    int col;
+                    const int64_t v = kc + lt;
+                    const int64_t e = v < nk ? wb + (compact ? (int64_t)w.klist[v] : v) : e_end;
+                    const int lr = edge_geometry<true>(a, w.rp, e, e_end, r0, nrows, eps, deps,
+                                                       Y, u4, col);
+                    w.row[lt] = lr;
+                    w.col[lt] = col;
+                    w.sj[lt] = lr >= 0 ? a.species[col] : 0;
+#pragma unroll
+                    for (int q = 1; q < TNLM; ++q) w.Y[lt][q - 1] = Y[q];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) w.u[lt][q] = u4[q];
+                    st_basis_row(w.B, 2 * lt, eps);
+                    st_basis_row(w.B, 2 * lt + 1, deps);
+                }
+                tc::fence_proxy_async();
+                tc::fence_before_sync();
+                wg_sync(g);
+                if (lt == 0) {   // MMA0: z1 = eps . W1^T, dz1 = (d eps/dr) . W1^T
+                    tc::fence_after_sync();
+                    mma_k32(tb, w.B, s.t.W1);
+                    tc::mma_commit(&w.mbar);
+                }
+                if (!wg_wait(w, phase, g)) { alive = false; break; }
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {   // value rows: silu(z1); tangent rows: silu'(z1) dz1
+                    float z[16];
+                    tc::tmem_ld16(tl + 16 * h, z);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float zv = __shfl_sync(0xffffffffu, z[q], lane & ~1);
+                        const float sg = sigmoid_fast(zv);
+                        z[q] = (lane & 1) ? sg * fmaf(zv, 1.f - sg, 1.f) * z[q] : zv * sg;
+                    }
+                    st_row_chunk(w.B, lt, 2 * h, z);
+                    st_row_chunk(w.B, lt, 2 * h + 1, z + 8);
+                }
+                tc::fence_proxy_async();
+                tc::fence_before_sync();
+                wg_sync(g);
+                if (lt == 0) {
+                    tc::fence_after_sync();
+                    mma_k64<64>(tb, w.B, s.t.W2);
+                    tc::mma_commit(&w.mbar);
+                }
+                if (!wg_wait(w, phase, g)) { alive = false; break; }
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {   // value rows: silu(z2); tangent rows: silu'(z2) dz2
+                    float z[16];
+                    tc::tmem_ld16(tl + 16 * h, z);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float zv = __shfl_sync(0xffffffffu, z[q], lane & ~1);
+                        const float sg = sigmoid_fast(zv);
+                        z[q] = (lane & 1) ? sg * fmaf(zv, 1.f - sg, 1.f) * z[q] : zv * sg;
+                    }
+                    st_row_chunk(w.B, lt, 2 * h, z);
+                    st_row_chunk(w.B, lt, 2 * h + 1, z + 8);
+                }
+                tc::fence_before_sync();
+                wg_sync(g);   // the a2 / da2 rows are complete (read below by hidden unit)
+                // this half's edges; V_j of the first is requested at once, each
+                // next one's while the current edge computes
+                const int e0 = 32 * half;
+                float vjc[TNLM], vjn[TNLM];
+                auto vj_ptr = [&](int e) -> const float* {
+                    const int lr = w.row[e];
+                    const int spk = w.spk[lr < 0 ? 0 : lr];
+                    return Vf + (((int64_t)w.col[e] * S + spk) * TNLM) * kH + hu;
+                };
+                {
+                    const float* p = vj_ptr(e0);
+#pragma unroll
+                    for (int q = 0; q < TNLM; ++q) vjc[q] = __ldg(p + q * kH);
+                }
+                auto edge_step = [&](int e, float (&vj)[TNLM], float (&vjnext)[TNLM]) -> bool {
+                    const int lr = w.row[e];
+                    if (lr < 0) return false;
+                    if (e + 1 < e0 + 32) {
+                        const float* p = vj_ptr(e + 1);
+#pragma unroll
+                        for (int q = 0; q < TNLM; ++q) vjnext[q] = __ldg(p + q * kH);
+                    }
+                    const int sj = w.sj[e];
+                    if (lr != cur) {
+                        if (cur >= 0) flush(cur);
+                        cur = lr;
+                        sk = w.spk[lr];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) FK(q) = FC(q) = 0.f;
+                        if (STRESS) {
+#pragma unroll
+                            for (int q = 0; q < 9; ++q) va[q] = 0.f;
+                        }
+                        if (S == 1) {
+                            const float* p = Vf + ((int64_t)(r0 + lr) * TNLM) * kH + hu;
+#pragma unroll
+                            for (int q = 0; q < TNLM; ++q) vk[q] = __ldg(p + q * kH);
+                        }
+                    }
+                    if (S != 1) {
+                        const float* p = Vf + (((int64_t)(r0 + lr) * S + sj) * TNLM) * kH + hu;
+#pragma unroll
+                        for (int q = 0; q < TNLM; ++q) vk[q] = __ldg(p + q * kH);
+                    }
+                    const float a2 = __bfloat162float(
+                        *reinterpret_cast<const __nv_bfloat16*>(Bb + tc::sw128_off(2 * e, hu)));
+                    const float da2 = __bfloat162float(
+                        *reinterpret_cast<const __nv_bfloat16*>(Bb + tc::sw128_off(2 * e + 1, hu)));
+                    float Y[TNLM];
+                    {
+                        const float4 y0 = *reinterpret_cast<const float4*>(&w.Y[e][0]);
+                        const float4 y1 = *reinterpret_cast<const float4*>(&w.Y[e][4]);
+                        Y[0] = 1.f;
+                        Y[1] = y0.x; Y[2] = y0.y; Y[3] = y0.z; Y[4] = y0.w;
+                        Y[5] = y1.x; Y[6] = y1.y; Y[7] = y1.z; Y[8] = y1.w;
+                    }
+                    // both directions of the edge (Y_lm(-u) = (-1)^l Y_lm(u))
+                    float D[TNLM];
+                    D[0] = vk[0] + vj[0];
+#pragma unroll
+                    for (int m = 1; m < 4; ++m) D[m] = vk[m] - vj[m];
+#pragma unroll
+                    for (int m = 4; m < 9; ++m) D[m] = vk[m] + vj[m];
+                    float wsum = D[0];
+#pragma unroll
+                    for (int m = 1; m < 9; ++m) wsum = fmaf(Y[m], D[m], wsum);
+                    const float gr = da2 * wsum;
+                    // dE/dY shares with the harmonics' factors (see sph_grad_prescaled)
+                    const float c1 = kS3 * a2, c2 = kS15 * a2;
+                    float gy[TNLM];
+                    gy[0] = 0.f;
+#pragma unroll
+                    for (int m = 1; m < 4; ++m) gy[m] = c1 * D[m];
+#pragma unroll
+                    for (int m = 4; m < 9; ++m) gy[m] = c2 * D[m];
+                    const float4 ue = *reinterpret_cast<const float4*>(&w.u[e][0]);
+                    const float u[3] = {ue.x, ue.y, ue.z};
+                    const float ir = ue.w;
+                    float v[3];
+                    sph_grad_prescaled(u, Y[3], gy, v);
+                    const float vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
+                    const float t = fmaf(-ir, vu, gr);
+                    float gq[3];   // this hidden unit's share of dE_pair/dd
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        gq[q] = fmaf(t, u[q], ir * v[q]);
+                        kadd(q, gq[q]);
+                    }
+                    if (STRESS) {
+                        const float r = 1.f / ir;
+#pragma unroll
+                        for (int p = 0; p < 3; ++p)
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) va[3 * p + q] = fmaf(gq[p], u[q] * r, va[3 * p + q]);
+                    }
+                    return true;
+                };
+#pragma unroll 1
+                for (int i = 0; i < 32; i += 2) {
+                    if (!edge_step(e0 + i, vjc, vjn)) break;
+                    if (!edge_step(e0 + i + 1, vjn, vjc)) break;
+                }
+                wg_sync(g);   // the B tile and edge records are rewritten by the next chunk
+            }
+            wb = we;
+        }
+        if (!alive) break;
+        if (cur >= 0) flush(cur);
+        wg_sync(g);
+        auto sum4 = [](const float2 (&p)[4][3], int q) {
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v += (double)p[k][q].x + (double)p[k][q].y;
+            return v;
+        };
+        if (lt < nrows * 3) {
+            const int lr = lt / 3, q = lt % 3;
+            a.frc[(r0 + lr) * 3 + q] += sum4(w.fpart[lr], q);
+        }
+        if (STRESS && lt < nrows * 9) {
+            const int lr = lt / 9, q = lt % 9;
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v += (double)w.vpart[lr][k][q].x + (double)w.vpart[lr][k][q].y;
+            a.vir[(int64_t)q * a.vir_stride + r0 + lr] += v;
+        }
+        wg_sync(g);
+    }
+    tc_teardown(s, phase, err, tid);
+}
+
 template <class S, int N, class K>
 int launch_tc(K kernel, const EdgeArgs& a, int rpg, int num_sms, cudaStream_t st) {
     const int64_t groups = (a.n + rpg - 1) / rpg;
@@ -1131,6 +1605,29 @@ int launch_edge_bwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int
     if (!(m.d.F == TF && m.d.lmax == TLMAX) || !a.w->W3sw || !a.err || !a.sched || !a.geo)
         return MP_ERR_UNSUPPORTED;
     if (a.n == 0) return MP_OK;
+    if (a.first && a.vfirst && a.species && a.emb && a.n_species >= 1) {
+        // layer 0 by hidden unit: V for the rows with a nonzero adjoint, zero
+        // for the rest, then the edge pass
+        const int64_t nv = a.n_recv > 0 ? a.n_recv : a.n;
+        const size_t per_atom = (size_t)a.n_species * TNLM * kH;
+        if (nv < a.n)
+            MP_CUDA_TRY(cudaMemsetAsync(a.vfirst + (size_t)nv * per_atom, 0,
+                                        sizeof(float) * (size_t)(a.n - nv) * per_atom, st));
+        if (nv > 0) {
+            const size_t vsm = sizeof(VSmem);
+            MP_CUDA_TRY(cudaFuncSetAttribute(k_v_first, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)vsm));
+            const int64_t tiles = (nv + VTA - 1) / VTA;
+            const int grid = (int)(tiles < num_sms ? tiles : num_sms);
+            k_v_first<<<grid, VTH, vsm, st>>>(nv, a.Alpha, a.emb, a.n_species, a.w->W3b, a.vfirst);
+            note_launch();
+            MP_CUDA_TRY(cudaGetLastError());
+        }
+        return a.vir ? launch_tc<SmemB0<true>, Bwd0Cfg<true>::NWG>(k_edge_bwd0_tc<true>, a, RPG_B,
+                                                                     num_sms, st)
+                     : launch_tc<SmemB0<false>, Bwd0Cfg<false>::NWG>(k_edge_bwd0_tc<false>, a,
+                                                                       RPG_B, num_sms, st);
+    }
     if (a.vir)
         return a.first ? launch_tc<SmemB<true, true>, BwdCfg<true, true>::NWG>(
                              k_edge_bwd_tc<true, true>, a, RPG_B, num_sms, st)

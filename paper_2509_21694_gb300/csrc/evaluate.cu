@@ -293,6 +293,7 @@ struct EvalBufs {
     double* vtot;     // [9] all sub-systems', in sub-system order
     float4* geo;      // BF16: per edge (u, r) of the current sub-system
     float4* split;    // BF16: the sub-system's positions as FP32 pairs (2 n)
+    float* vfirst;    // BF16 layer-0 adjoint: hidden-unit vectors [n][S][NLM][kH], or null
 };
 
 // Rows a pass must cover: atoms within `hops` hops of a root (a prefix of
@@ -348,6 +349,10 @@ int run_subsystem(mp_ctx* ctx, const SubSys& ss, const EvalBufs& b, const EdgeCo
     ea.vir_stride = n;
     if (b.vloc) MP_CUDA_TRY(cudaMemsetAsync(b.vloc, 0, sizeof(double) * 9 * n, st));
     ea.sched = ctx->ws.sched.as<int>();
+    ea.species = sp;
+    ea.emb = m.emb;
+    ea.n_species = m.d.n_species;
+    ea.vfirst = b.vfirst;
     if (precision == MP_BF16) {   // edge geometry once for all of this sub-system's passes
         ea.geo = b.geo;
         TimerScope ts(ctx, MP_TIMER_PARTITION, ss.n_edges, n);
@@ -556,10 +561,15 @@ int evaluate(mp_ctx* ctx, const double* d_pos, const int32_t* d_species, const G
     b.eloc = ws.eatom.as<double>();
     b.vloc = b.vsum = b.vtot = nullptr;
     b.geo = b.split = nullptr;
+    b.vfirst = nullptr;
     if (precision == MP_BF16) {
         MP_TRY(ws.geo.reserve(sizeof(float4) * (emax + 1 + 2 * nmax)));
         b.geo = ws.geo.as<float4>();
         b.split = b.geo + emax + 1;
+        if (F == 128 && m.d.lmax == 2) {
+            MP_TRY(ws.vfirst.reserve(sizeof(float) * (size_t)nmax * m.d.n_species * NLM * kH));
+            b.vfirst = ws.vfirst.as<float>();
+        }
     }
     if (d_stress) {
         MP_TRY(ws.vir.reserve(sizeof(double) * (9 * nmax + 18)));

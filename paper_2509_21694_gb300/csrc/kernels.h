@@ -36,6 +36,13 @@ struct EdgeArgs {
     // ends are both >= n_recv has zero adjoint on both sides and may be
     // skipped (<= 0: every row is a receiver)
     int64_t n_recv;
+    // BF16 layer-0 adjoint (tensor-core path): local species of every row, the
+    // embedding table [S][F], and scratch for the per-atom hidden-unit
+    // vectors V [n][S][NLM][H] (null: the channel-wise kernel is used)
+    const int32_t* species;
+    const float* emb;
+    int n_species;
+    float* vfirst;
 };
 
 // (u_x, u_y, u_z, r) of every edge of a CSR over n rows, for the tensor-core
