@@ -1034,26 +1034,35 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
 // receiver row exactly as in the channel-wise kernel, the hidden units
 // taking the place of the channels in the per-row sums.
 
-constexpr int VTA = 8;            // atoms per tile of k_v_first
-constexpr int VTH = 512;          // its threads: 16 hidden quads x 8 atoms x 4 (l, m) groups
+constexpr int VTA = 16;           // atoms per tile of k_v_first
+constexpr int VTH = 256;          // its threads: 16 hidden-unit quads x 16 atoms
+constexpr int VCB = 16;           // channels summed in FP32 before the compensated addition
+constexpr int VXS = TNLM * 128 + 4;   // floats per atom row of the staged alpha (padded)
 struct alignas(16) VSmem {
     float W[3][128][kH];          // W3 blocks of paths R0, R1a, R2a (FP32 of the BF16 values) x Emb[s]
-    float X[TNLM][128][VTA + 1];  // alpha of the tile's atoms, [lm][c][atom] (padded)
+    float X[VTA][VXS];            // alpha of the tile's atoms, [atom][lm][c]
 };
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(smem_dst)),
+                 "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // V[a][s][lm][h] for atoms a < nrows (the rows with a nonzero adjoint).  The
-// CTA keeps the three weight blocks in shared memory and loops over tiles of
-// VTA atoms; a thread owns four hidden units of one atom and two or three
-// (l, m) rows: {0, 1, 2}, {3, 4}, {5, 6}, {7, 8}.
+// CTA keeps the three weight blocks, scaled by the species' embedding, in
+// shared memory and loops over tiles of VTA atoms; a thread owns four hidden
+// units of one atom for all nine (l, m) rows (36 sums), so that each
+// shared-memory load feeds four or twelve multiply-adds.
 __global__ void __launch_bounds__(VTH, 1)
     k_v_first(int64_t nrows, const float* __restrict__ alpha, const float* __restrict__ emb,
               int S, const __nv_bfloat16* __restrict__ W3b, float* __restrict__ V) {
     extern __shared__ float4 vsm_raw[];
     VSmem& s = *reinterpret_cast<VSmem*>(vsm_raw);
     const int tid = threadIdx.x;
-    const int h4 = tid & 15, ta = (tid >> 4) & 7, grp = tid >> 7;
-    const int lm0 = grp == 0 ? 0 : 1 + 2 * grp;   // 0, 3, 5, 7
-    const int nlm = grp == 0 ? 3 : 2;
+    const int h4 = tid & 15, ta = tid >> 4;
     const int64_t ntiles = (nrows + VTA - 1) / VTA;
     for (int sp = 0; sp < S; ++sp) {
         __syncthreads();   // the previous species' weights consumed
@@ -1068,68 +1077,68 @@ __global__ void __launch_bounds__(VTH, 1)
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const int64_t a0 = tile * VTA;
             __syncthreads();   // weights ready; the previous X consumed
-            for (int q = tid; q < VTA * TNLM * 128; q += VTH) {
-                const int a = q / (TNLM * 128), lm = (q / 128) % TNLM, c = q & 127;
+            // the tile's alpha rows, 16 bytes per asynchronous copy, all in flight at once
+            for (int q = tid; q < VTA * (TNLM * 128 / 4); q += VTH) {
+                const int a = q / (TNLM * 32), off = (q % (TNLM * 32)) * 4;
                 const int64_t atom = a0 + a;
-                s.X[lm][c][a] = atom < nrows ? __ldg(&alpha[(atom * TNLM + lm) * 128 + c]) : 0.f;
+                if (atom < nrows)
+                    cp_async16(&s.X[a][off], alpha + atom * (TNLM * 128) + off);
+                else
+                    *reinterpret_cast<float4*>(&s.X[a][off]) = make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            cp_async_wait_all();
             __syncthreads();
-            // the channel sum in blocks of 16 (FP32 multiply-adds), the block
-            // sums added into an unevaluated pair hi + lo by two-sum: a per-
-            // partition adjoint's V stays within a few roundings of its exact
-            // value, so that partition sums of V agree with the whole system's
-            float hi[3][4], lo[3][4];
+            // the channel sum in blocks of VCB (packed FP32 multiply-adds, two
+            // hidden units per instruction, each rounded as a scalar FMA), the
+            // block sums added into an unevaluated pair hi + lo by two-sum: a
+            // per-partition adjoint's V stays within a few roundings of its
+            // exact value, so that partition sums of V agree with the whole
+            // system's
+            float hi[TNLM][4], lo[TNLM][4];
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+            for (int i = 0; i < TNLM; ++i)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) hi[i][k] = lo[i][k] = 0.f;
 #pragma unroll 1
-            for (int cb = 0; cb < 128; cb += 16) {
-                float acc[3][4];
+            for (int cb = 0; cb < 128; cb += VCB) {
+                float2 acc[TNLM][2];
 #pragma unroll
-                for (int i = 0; i < 3; ++i)
+                for (int i = 0; i < TNLM; ++i) acc[i][0] = acc[i][1] = make_float2(0.f, 0.f);
+#pragma unroll 2
+                for (int c = cb; c < cb + VCB; ++c) {
+                    float4 wv[3];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
-#pragma unroll 4
-                for (int c = cb; c < cb + 16; ++c) {
+                    for (int p = 0; p < 3; ++p) wv[p] = *reinterpret_cast<const float4*>(&s.W[p][c][4 * h4]);
 #pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        if (i < nlm) {
-                            const int lm = lm0 + i;
-                            const int path = lm == 0 ? 0 : (lm < 4 ? 1 : 2);
-                            const float4 wv = *reinterpret_cast<const float4*>(&s.W[path][c][4 * h4]);
-                            const float x = s.X[lm][c][ta];
-                            acc[i][0] = fmaf(x, wv.x, acc[i][0]);
-                            acc[i][1] = fmaf(x, wv.y, acc[i][1]);
-                            acc[i][2] = fmaf(x, wv.z, acc[i][2]);
-                            acc[i][3] = fmaf(x, wv.w, acc[i][3]);
-                        }
+                    for (int i = 0; i < TNLM; ++i) {
+                        const float4 w4 = wv[i == 0 ? 0 : (i < 4 ? 1 : 2)];
+                        const float x = s.X[ta][i * 128 + c];
+                        const float2 xx = make_float2(x, x);
+                        acc[i][0] = __ffma2_rn(xx, make_float2(w4.x, w4.y), acc[i][0]);
+                        acc[i][1] = __ffma2_rn(xx, make_float2(w4.z, w4.w), acc[i][1]);
                     }
                 }
 #pragma unroll
-                for (int i = 0; i < 3; ++i)
+                for (int i = 0; i < TNLM; ++i) {
+                    const float blk[4] = {acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y};
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const float sum = __fadd_rn(hi[i][k], acc[i][k]);
+                        const float sum = __fadd_rn(hi[i][k], blk[k]);
                         const float bb = __fsub_rn(sum, hi[i][k]);
                         const float err = __fadd_rn(__fsub_rn(hi[i][k], __fsub_rn(sum, bb)),
-                                                    __fsub_rn(acc[i][k], bb));
+                                                    __fsub_rn(blk[k], bb));
                         hi[i][k] = sum;
                         lo[i][k] = __fadd_rn(lo[i][k], err);
                     }
+                }
             }
-            float acc[3][4];
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) acc[i][k] = __fadd_rn(hi[i][k], lo[i][k]);
             const int64_t atom = a0 + ta;
             if (atom < nrows) {
 #pragma unroll
-                for (int i = 0; i < 3; ++i)
-                    if (i < nlm)
-                        *reinterpret_cast<float4*>(&V[((atom * S + sp) * TNLM + lm0 + i) * kH + 4 * h4]) =
-                            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                for (int i = 0; i < TNLM; ++i)
+                    *reinterpret_cast<float4*>(&V[((atom * S + sp) * TNLM + i) * kH + 4 * h4]) =
+                        make_float4(__fadd_rn(hi[i][0], lo[i][0]), __fadd_rn(hi[i][1], lo[i][1]),
+                                    __fadd_rn(hi[i][2], lo[i][2]), __fadd_rn(hi[i][3], lo[i][3]));
             }
         }
     }
