@@ -74,12 +74,14 @@ def parse():
     return ap.parse_args()
 
 
-# DRAM read + write bytes per processed edge of the tensor-core edge adjoint,
-# averaged over its layer-0 and layer-1 launches, from one ncu capture on
-# 131,072 atoms, scaled by the edges of a launch.  The figure belongs to the
-# kernel sources whose hash is stored beside it: once those sources change,
-# the line reports traffic null until the counters are taken again.
-TRAFFIC_BYTES_PER_EDGE_BF16 = {"bwd": (477.2, "bea0abc20d55becc")}
+# DRAM read + write bytes per processed edge of the tensor-core edge adjoint
+# (its layer-1 launch, its layer-0 launch and the layer-0 per-atom V that
+# runs inside the same timed call), from one ncu capture on 131,072 atoms,
+# over the edges of the two launches; scaled by the edges of a launch.  The
+# figure belongs to the kernel sources whose hash is stored beside it: once
+# those sources change, the line reports traffic null until the counters are
+# taken again.
+TRAFFIC_BYTES_PER_EDGE_BF16 = {"bwd": (412.6, "a55601ce67599318")}
 TRAFFIC_SOURCES = ("edge_bf16.cu", "edge_math.cuh", "tc.cuh", "kernels.h", "common.cuh")
 
 
@@ -278,28 +280,47 @@ class Clocks:
 #     dY/du contraction (v, 9 multiply-adds) and the pair-gradient
 #       share t u + v / r                                             37
 #                                                            total   170
-#   adjoint, layer 0 (no l >= 1 inputs): P_lm 24, P.Y 16, dE/dY 10,
-#     dR contraction 8, dY/du and pair gradient 37             total    95
+#   adjoint, layer 0 (no l >= 1 inputs), channel-wise (FP32 path):
+#     P_lm 24, P.Y 16, dE/dY 10, dR contraction 8, dY/du and pair
+#     gradient 37                                              total    95
 #   forward, layer >= 1: A0 2, l = 1: 13, l = 2: 21            total    36
 #   forward, layer 0:                                          total    20
 # (all three radial-MLP layers run on the tensor cores; the first, K = 8,
 # as one zero-padded K = 16 MMA, counted at its algorithmic K = 8).
+# The BF16 layer-0 adjoint runs by hidden unit instead (its sender features
+# are species embeddings, so the channel sums factor through W3): per edge
+# and hidden unit, D_lm = Vk -+ Vj 9, sum_lm Y_lm D_lm 16, the dE/dr and
+# dE/dY shares 11, dY/du contraction 18, v.u and t 7, the pair-gradient
+# share 9 and its addition to the row sum 3: 73; plus, per atom with a
+# nonzero adjoint and species s, V = (W3 Emb_s)^T alpha: 9 x 64 x 128
+# multiply-adds.
 FP32_FLOPS_PER_CHANNEL = {("bwd", False): 170, ("bwd", True): 95,
                           ("fwd", False): 36, ("fwd", True): 20}
+BWD0_FLOPS_PER_HIDDEN = 73
 
 
-def edge_fp32_flops(kind: str, F: int, first: bool) -> float:
+def edge_fp32_flops(kind: str, F: int, first: bool, hidden_form: bool = False) -> float:
+    if hidden_form and kind == "bwd" and first:
+        return float(BWD0_FLOPS_PER_HIDDEN * 64)
     return float(FP32_FLOPS_PER_CHANNEL[(kind, first)] * F)
 
 
-def edge_tensor_flops(kind: str, F: int, lmax: int, first: bool) -> float:
+def v_first_flops(alpha_rows: float, n_species: int, F: int = 128, nlm: int = 9,
+                  H: int = 64) -> float:
+    """FP32 FLOPs of the per-atom vectors V of the hidden-unit layer-0 adjoint."""
+    return 2.0 * nlm * H * F * n_species * alpha_rows
+
+
+def edge_tensor_flops(kind: str, F: int, lmax: int, first: bool,
+                      hidden_form: bool = False) -> float:
     """BF16 tensor-core FLOPs per edge: the three radial-MLP layers (NB x H,
     H x H and H x paths F), for the value row and, in the adjoint, its
-    r-tangent row."""
+    r-tangent row; the hidden-unit layer-0 adjoint runs the first two only."""
     H, NB = 64, 8
     n_paths = (1 + lmax) if first else (1 + 2 * lmax)
     rows = 2 if kind == "bwd" else 1
-    return 2.0 * rows * (NB * H + H * H + H * n_paths * F)
+    last = 0 if (hidden_form and kind == "bwd" and first) else H * n_paths * F
+    return 2.0 * rows * (NB * H + H * H + last)
 
 
 def load_peaks():
@@ -435,10 +456,15 @@ def run_ours(args, rank, world):
                 # two resources: the tensor pipe (radial layers 2 and 3) and the
                 # FP32 pipe (radial layer 1 and the per-channel epilogue); the
                 # bound is the one whose algorithmic work takes longer at peak
-                tfl = (t0["edges"] * edge_tensor_flops(kind, 128, 2, True) +
+                # layer 0 of the adjoint: hidden-unit form, with its per-atom
+                # V (launched inside the same timed call; its atoms are the
+                # layer-0 node adjoint's rows)
+                tfl = (t0["edges"] * edge_tensor_flops(kind, 128, 2, True, True) +
                        t1["edges"] * edge_tensor_flops(kind, 128, 2, False)) / launches_all
-                afl = (t0["edges"] * edge_fp32_flops(kind, 128, True) +
+                afl = (t0["edges"] * edge_fp32_flops(kind, 128, True, True) +
                        t1["edges"] * edge_fp32_flops(kind, 128, False)) / launches_all
+                if kind == "bwd":
+                    afl += v_first_flops(timing["node_bwd_l0"]["atoms"], d.n_species) / launches_all
                 tpk = peaks.get("bf16_tflops_sustained", 1700.0)
                 src_hash = kernel_source_hash()
                 per_edge, measured_on = TRAFFIC_BYTES_PER_EDGE_BF16.get(kind, (None, None))

@@ -44,6 +44,11 @@
 // (later-layer forward) or one (adjoint) edges at a time.
 // The MLP's hidden activations use the hardware tanh for the sigmoid: they
 // are rounded to BF16 for the next contraction anyway.
+// The adjoint of layer 0 runs by hidden unit instead (k_v_first and
+// k_edge_bwd0_tc, below): there the senders' features are species
+// embeddings, so its channel sums factor through the last radial layer and
+// are formed once per atom; the channel-wise layer-0 adjoint remains for a
+// caller that provides no scratch for those per-atom vectors.
 // One thread issues the MMAs; completion is signalled through an mbarrier
 // whose waits are bounded (clock64): on a timeout the warpgroup sets an
 // error bit, stops, and the CTA frees its tensor memory and returns.
@@ -1162,21 +1167,18 @@ struct alignas(1024) WgState0 {
     int spk[RPG_B];                  // species of the group's rows
     float2 fpart[RPG_B][4][3];
     float2 vpart[RPG_B][4][STRESS ? 9 : 1];
-    float fkc[6][128];               // per thread: compensated row force sums (fk, fc)
     int64_t rp[RPG_B + 1];
     int64_t next_grp;
     uint64_t mbar;
     int abort;
 };
 
-// Six warpgroups at 80 registers (the compensated row force sums in shared
-// memory), four with the stress (virial partials in registers).
+// Six warpgroups at 80 registers, four with the stress (virial partials).
 template <bool STRESS>
 struct Bwd0Cfg {
     static constexpr int NWG = STRESS ? 4 : 6;
     static constexpr int NTH = 128 * NWG;
     static constexpr int COLS = 64;   // D0 and D1 (128 rows x 64 hidden units)
-    static constexpr bool FKS = !STRESS;
 };
 template <class WG, int N>
 struct SmemT0 {
@@ -1228,16 +1230,12 @@ __global__ void __launch_bounds__((Bwd0Cfg<STRESS>::NTH), 1)
         // a compensated sum (fk, fc): a hidden unit's share of an edge is a
         // sum over all channels, larger than a channel's share, so it is not
         // first summed over several edges in plain FP32
-        float fk_r[3] = {0.f, 0.f, 0.f}, fc_r[3] = {0.f, 0.f, 0.f};
-        float* __restrict__ fkc = &w.fkc[0][lt];
-        auto FK = [&](int q) -> float& { return Cfg::FKS ? fkc[q * 128] : fk_r[q]; };
-        auto FC = [&](int q) -> float& { return Cfg::FKS ? fkc[(3 + q) * 128] : fc_r[q]; };
+        float fk[3] = {0.f, 0.f, 0.f}, fc[3] = {0.f, 0.f, 0.f};
         auto kadd = [&](int q, float gq) {
-            const float fkq = FK(q), fcq = FC(q);
-            const float y = gq - fcq;
-            const float t = fkq + y;
-            FC(q) = (t - fkq) - y;
-            FK(q) = t;
+            const float y = gq - fc[q];
+            const float t = fk[q] + y;
+            fc[q] = (t - fk[q]) - y;
+            fk[q] = t;
         };
         float va[STRESS ? 9 : 1];
 #pragma unroll
@@ -1245,7 +1243,7 @@ __global__ void __launch_bounds__((Bwd0Cfg<STRESS>::NTH), 1)
         auto flush = [&](int lr) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {   // this thread's share is fk - fc
-                float hi = FK(q), lo = -FC(q);
+                float hi = fk[q], lo = -fc[q];
                 warp_sum_pair(hi, lo);
                 if (lane == 0) w.fpart[lr][warp & 3][q] = make_float2(hi, lo);
             }
@@ -1389,7 +1387,7 @@ __global__ void __launch_bounds__((Bwd0Cfg<STRESS>::NTH), 1)
                         cur = lr;
                         sk = w.spk[lr];
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) FK(q) = FC(q) = 0.f;
+                        for (int q = 0; q < 3; ++q) fk[q] = fc[q] = 0.f;
                         if (STRESS) {
 #pragma unroll
                             for (int q = 0; q < 9; ++q) va[q] = 0.f;

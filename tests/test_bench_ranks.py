@@ -55,6 +55,13 @@ def test_roofline_accounting():
     assert bench.edge_tensor_flops("bwd", F, 2, True) == 2 * 2 * (8 * H + H * H + H * 3 * F)
     assert bench.edge_fp32_flops("bwd", F, False) == 170 * F
     assert bench.edge_fp32_flops("fwd", F, True) == 20 * F
+    # the BF16 layer-0 adjoint by hidden unit: no third radial layer on the
+    # tensor cores, 73 FLOP per hidden unit and edge, and per atom with a
+    # nonzero adjoint the 9 x 64 x 128 multiply-adds of V per species
+    assert bench.edge_tensor_flops("bwd", F, 2, True, True) == 2 * 2 * (8 * H + H * H)
+    assert bench.edge_fp32_flops("bwd", F, True, True) == 73 * H
+    assert bench.edge_fp32_flops("bwd", F, True) == 95 * F
+    assert bench.v_first_flops(10, 2) == 2 * 9 * H * F * 2 * 10
     row, lm = 4 * F, 4 * F * 8
     # forward, layer 0 of two: read A (9 rows) and h0, write S and h' (9 rows)
     assert bench.node_bytes_per_atom("fwd", True, False) == (row + lm) + row + row + (row + lm)
