@@ -1490,6 +1490,329 @@ __global__ void __launch_bounds__((Bwd0Cfg<STRESS>::NTH), 1)
     tc_teardown(s, phase, err, tid);
 }
 
+// ------------------------------------------ layer-0 forward by hidden unit --
+//
+// The same factorisation as the layer-0 adjoint above, in the forward
+// direction: with h0_j = Emb[s_j] and R_q = W3_q a2,
+//   A_k[c, lm] = N_avg^-1 sum_e R_q(l)(e)[c] Emb[s_j][c] Y_lm(e)
+//             = N_avg^-1 sum_s Emb[s][c] sum_h W3_q(l)[c][h] G_k[s][lm][h],
+//   G_k[s][lm][h] = sum_{e in row k, s_j = s} a2_e[h] Y_lm(e).
+// k_edge_fwd0_tc runs the geometry and the first two radial layers of each
+// edge and sums G per receiver row (thread = hidden unit and half of the
+// (l, m) rows, no third MMA, no per-channel work); k_a_first_tc then forms A
+// from G on the tensor cores, 16 atoms per MMA, with G split into three
+// BF16 parts so that the product keeps FP32 accuracy.
+
+constexpr int SMAX0 = 3;          // species handled by the hidden-unit layer 0
+
+template <int S>
+struct alignas(1024) WgStateF0 {
+    __nv_bfloat16 B[128 * 64];       // basis rows, then the a1 and a2 tiles (row = edge)
+    float Y[SCF][TNLM - 1];          // Y_lm for lm = 1..8
+    int row[SCF], sj[SCF];           // receiver row (-1: past the end), sender species
+    int64_t rp[RPG + 1];
+    int64_t next_grp;
+    uint64_t mbar;
+    int abort;
+};
+template <int S>
+struct F0Cfg {
+    static constexpr int NWG = 6;
+    static constexpr int NTH = 128 * NWG;
+    static constexpr int COLS = 64;   // D0 and D1 (128 edges x 64 hidden units)
+};
+template <int S>
+using SmemF0 = SmemT0<WgStateF0<S>, F0Cfg<S>::NWG>;
+static_assert(smem_fits<SmemF0<1>>() && smem_fits<SmemF0<SMAX0>>(),
+              "shared memory of the layer-0 hidden-unit forward");
+
+// G of every row of the pass (zero for a row without edges).  Thread lt of a
+// warpgroup owns hidden unit lt & 63 and the (l, m) rows 0..4 (lt < 64) or
+// 5..8, and runs through all edges of a super-chunk in order, so each row's
+// sum is formed by one thread in edge order (the same in every partition).
+template <int S>
+__global__ void __launch_bounds__((F0Cfg<S>::NTH), 1)
+    k_edge_fwd0_tc(EdgeArgs a, LayerW wl, int64_t n_groups, int* err) {
+    using Cfg = F0Cfg<S>;
+    extern __shared__ unsigned char smem_raw[];
+    auto& s = smem_as<SmemF0<S>>(smem_raw);
+    const int tid = threadIdx.x, g = tid >> 7, lt = tid & 127, warp = tid >> 5, lane = tid & 31;
+    const int hu = lt & 63, grp = lt >> 6;
+    const int lm0 = grp ? 5 : 0;
+    constexpr int NL = 5;              // (l, m) rows per thread (4 used by the second half)
+    auto& w = s.wg[g];
+    float* __restrict__ Gout = a.vfirst;
+    tc_setup<Cfg::NTH>(s, wl, 0, true, tid);
+    const uint32_t tb = s.taddr + Cfg::COLS * g;
+    const uint32_t tl = tb + ((uint32_t)(32 * (warp & 3)) << 16);
+    uint32_t phase = 0;
+    bool alive = true;
+    const unsigned char* Bb = reinterpret_cast<const unsigned char*>(w.B);
+    const int nlm = grp ? 4 : 5;
+
+    for (int64_t gi = (int64_t)blockIdx.x * Cfg::NWG + g; gi < n_groups && alive;
+         gi = next_group<Cfg::NWG>(w, a, g, lt)) {
+        const int64_t r0 = gi * RPG_F;
+        const int nrows = (int)min((int64_t)RPG_F, a.n - r0);
+        if (lt <= nrows) w.rp[lt] = a.row_ptr[r0 + lt];
+        wg_sync(g);
+        const int64_t e_beg = w.rp[0], e_end = w.rp[nrows];
+        float acc[S][NL];
+#pragma unroll
+        for (int q = 0; q < S; ++q)
+#pragma unroll
+            for (int i = 0; i < NL; ++i) acc[q][i] = 0.f;
+        int cur = -1, next = 0;
+        auto write_row = [&](int lr, bool zero) {
+            float* __restrict__ o = Gout + ((r0 + lr) * S * TNLM + lm0) * kH + hu;
+#pragma unroll
+            for (int q = 0; q < S; ++q)
+#pragma unroll
+                for (int i = 0; i < NL; ++i)
+                    if (i < nlm) o[(q * TNLM + i) * kH] = zero ? 0.f : acc[q][i];
+        };
+        for (int64_t sc = e_beg; sc < e_end && alive; sc += SCF) {
+            {   // geometry of edge lt; its radial basis -> tile row lt
+                float eps[kNB], deps[kNB], Y[TNLM], u4[4];
+                int col;
+                const int lr = edge_geometry<false>(a, w.rp, sc + lt, e_end, r0, nrows, eps, deps,
+                                                    Y, u4, col);
+                w.row[lt] = lr;
+                w.sj[lt] = (S > 1 && lr >= 0) ? a.species[col] : 0;
+#pragma unroll
+                for (int q = 1; q < TNLM; ++q) w.Y[lt][q - 1] = Y[q];
+                st_basis_row(w.B, lt, eps);
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            wg_sync(g);
+            if (lt == 0) {   // MMA0: z1 = eps . W1^T
+                tc::fence_after_sync();
+                mma_k32(tb, w.B, s.t.W1);
+                tc::mma_commit(&w.mbar);
+            }
+            if (!wg_wait(w, phase, g)) { alive = false; break; }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {   // a1 = silu(z1): lane lt holds tile row lt
+                float z[16];
+                tc::tmem_ld16(tl + 16 * h, z);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 16; ++q) z[q] = z[q] * sigmoid_fast(z[q]);
+                st_row_chunk(w.B, lt, 2 * h, z);
+                st_row_chunk(w.B, lt, 2 * h + 1, z + 8);
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            wg_sync(g);
+            if (lt == 0) {
+                tc::fence_after_sync();
+                mma_k64<64>(tb, w.B, s.t.W2);
+                tc::mma_commit(&w.mbar);
+            }
+            if (!wg_wait(w, phase, g)) { alive = false; break; }
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {   // a2 = silu(z2)
+                float z[16];
+                tc::tmem_ld16(tl + 16 * h, z);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 16; ++q) z[q] = z[q] * sigmoid_fast(z[q]);
+                st_row_chunk(w.B, lt, 2 * h, z);
+                st_row_chunk(w.B, lt, 2 * h + 1, z + 8);
+            }
+            tc::fence_before_sync();
+            wg_sync(g);   // the a2 rows are complete (read below by hidden unit)
+#pragma unroll 2
+            for (int e = 0; e < SCF; ++e) {
+                const int lr = w.row[e];
+                if (lr < 0) break;
+                if (lr != cur) {
+                    if (cur >= 0) {
+                        write_row(cur, false);
+                        next = cur + 1;
+                    }
+                    for (int q = next; q < lr; ++q) write_row(q, true);
+                    next = lr;
+                    cur = lr;
+#pragma unroll
+                    for (int q = 0; q < S; ++q)
+#pragma unroll
+                        for (int i = 0; i < NL; ++i) acc[q][i] = 0.f;
+                }
+                const float a2 = __bfloat162float(
+                    *reinterpret_cast<const __nv_bfloat16*>(Bb + tc::sw128_off(e, hu)));
+                // this thread's (l, m) rows: Y_0 = 1, Y_1..Y_4 or Y_5..Y_8
+                float y[NL];
+                {
+                    const float4 yv = *reinterpret_cast<const float4*>(&w.Y[e][grp ? 4 : 0]);
+                    if (grp) {
+                        y[0] = yv.x; y[1] = yv.y; y[2] = yv.z; y[3] = yv.w; y[4] = 0.f;
+                    } else {
+                        y[0] = 1.f; y[1] = yv.x; y[2] = yv.y; y[3] = yv.z; y[4] = yv.w;
+                    }
+                }
+                const int sp = S > 1 ? w.sj[e] : 0;
+#pragma unroll
+                for (int q = 0; q < S; ++q) {
+                    if (S == 1 || q == sp) {
+#pragma unroll
+                        for (int i = 0; i < NL; ++i) acc[q][i] = fmaf(a2, y[i], acc[q][i]);
+                    }
+                }
+            }
+            wg_sync(g);   // the tile and edge records are rewritten by the next chunk
+        }
+        if (!alive) break;
+        if (cur >= 0) {
+            write_row(cur, false);
+            next = cur + 1;
+        }
+        for (int q = next; q < nrows; ++q) write_row(q, true);
+        wg_sync(g);
+    }
+    tc_teardown(s, phase, err, tid);
+}
+
+// A of 16 atoms per tile: D[128 x 16] = W3_q(l) . (G_s[lm] in three BF16
+// parts)^T for every (l, m) and species, then A[atom][lm][c] =
+// N_avg^-1 sum_s Emb[s][c] D_s[lm][c][atom].
+constexpr int AF_NT = 16;         // atoms per tile (MMA N)
+constexpr int AF_NTH = 512;       // threads: 16 atoms x 32 in the load phase
+template <int S>
+struct alignas(1024) AfSmem {
+    __nv_bfloat16 W3[3][128 * 64];              // paths R0, R1a, R2a (swizzled images)
+    __nv_bfloat16 X[TNLM][S][3][AF_NT * 64];    // G parts: (l, m), species, part
+    uint64_t mbar;
+    uint32_t taddr;
+    int abort;
+};
+template <int S>
+constexpr bool af_fits() { return sizeof(AfSmem<S>) + 1024 <= 232448; }
+static_assert(af_fits<1>() && af_fits<SMAX0>(), "shared memory of k_a_first_tc");
+static_assert(TNLM * SMAX0 * AF_NT <= TM_COLS, "tensor memory of k_a_first_tc");
+
+// D[tmem, 128 x N] (+)= A(128 x 64 tile) . B(N x 64 tile)^T, four K = 16 steps.
+template <int N>
+__device__ __forceinline__ void mma_k64_acc(uint32_t d, const __nv_bfloat16* A,
+                                            const __nv_bfloat16* B, bool acc) {
+    const uint64_t ad = tc::desc_sw128(tc::smem_u32(A));
+    const uint64_t bd = tc::desc_sw128(tc::smem_u32(B));
+    constexpr uint32_t idesc = tc::idesc_bf16(128, N);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+        tc::mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc, (acc || kk > 0) ? 1u : 0u);
+}
+
+template <int S>
+__global__ void __launch_bounds__(AF_NTH, 1)
+    k_a_first_tc(int64_t n, const float* __restrict__ G, const float* __restrict__ emb,
+                 const __nv_bfloat16* __restrict__ W3sw, float inv_navg,
+                 float* __restrict__ Aout, int64_t n_tiles, int* err) {
+    extern __shared__ unsigned char smem_raw[];
+    auto& s = smem_as<AfSmem<S>>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ia = tid >> 5, q = tid & 31;            // load phase: atom, float4 slot
+    const int lq = warp & 3, ag = warp >> 2;          // epilogue: lane quarter, atom group
+    const int c = 32 * lq + lane;
+    for (int p = 0; p < 3; ++p) {
+        const int blk = p == 0 ? 0 : 2 * p - 1;
+        const uint4* src = reinterpret_cast<const uint4*>(W3sw + (size_t)blk * 128 * 64);
+        uint4* dst = reinterpret_cast<uint4*>(s.W3[p]);
+        for (int k = tid; k < 128 * 64 * 2 / 16; k += AF_NTH) dst[k] = __ldg(&src[k]);
+    }
+    if (tid == 0) {
+        tc::mbar_init(&s.mbar, 1);
+        s.abort = 0;
+    }
+    if (warp == 0) tc::tmem_alloc<TM_COLS>(&s.taddr);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    float es[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) es[k] = __ldg(&emb[k * 128 + c]);
+    uint32_t phase = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t atom = tile * AF_NT + ia;
+        // G of atom ia in three BF16 parts (each the rounding of what the
+        // previous parts leave), into the swizzled K-major operand tiles
+        for (int r = q; r < S * TNLM * 16; r += 32) {
+            const int sp = r / (TNLM * 16), lm = (r / 16) % TNLM, h4 = r & 15;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (atom < n)
+                v = __ldg(reinterpret_cast<const float4*>(G + ((atom * S + sp) * TNLM + lm) * kH) + h4);
+            float rr[4] = {v.x, v.y, v.z, v.w};
+            const uint32_t off = ia * 128 + ((((h4 >> 1) ^ (ia & 7)) & 7) << 4) + ((h4 & 1) << 3);
+#pragma unroll
+            for (int part = 0; part < 3; ++part) {
+                const __nv_bfloat162 lo = __floats2bfloat162_rn(rr[0], rr[1]);
+                const __nv_bfloat162 hi = __floats2bfloat162_rn(rr[2], rr[3]);
+                rr[0] -= __low2float(lo);
+                rr[1] -= __high2float(lo);
+                rr[2] -= __low2float(hi);
+                rr[3] -= __high2float(hi);
+                uint2 u;
+                u.x = *reinterpret_cast<const uint32_t*>(&lo);
+                u.y = *reinterpret_cast<const uint32_t*>(&hi);
+                *reinterpret_cast<uint2*>(reinterpret_cast<unsigned char*>(s.X[lm][sp][part]) + off) = u;
+            }
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+#pragma unroll 1
+            for (int lm = 0; lm < TNLM; ++lm) {
+                const int path = lm == 0 ? 0 : (lm < 4 ? 1 : 2);
+                for (int sp = 0; sp < S; ++sp) {
+                    const uint32_t d = s.taddr + AF_NT * (lm * S + sp);
+#pragma unroll
+                    for (int part = 0; part < 3; ++part)
+                        mma_k64_acc<AF_NT>(d, s.W3[path], s.X[lm][sp][part], part > 0);
+                }
+            }
+            tc::mma_commit(&s.mbar);
+        }
+        if (tc::mbar_wait(&s.mbar, phase))
+            phase ^= 1u;
+        else
+            s.abort = 1;
+        __syncthreads();
+        tc::fence_after_sync();
+        if (s.abort) break;
+        const int64_t i0 = tile * AF_NT + 4 * ag;
+        const uint32_t tcol = s.taddr + ((uint32_t)(32 * lq) << 16) + 4 * ag;
+#pragma unroll 1
+        for (int lm = 0; lm < TNLM; ++lm) {
+            float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int sp = 0; sp < S; ++sp) {
+                float dv[4];
+                tc::tmem_ld4(tcol + AF_NT * (lm * S + sp), dv);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int r = 0; r < 4; ++r) o[r] = fmaf(es[sp], dv[r], o[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (i0 + r < n) Aout[((i0 + r) * TNLM + lm) * 128 + c] = o[r] * inv_navg;
+        }
+        tc::fence_before_sync();
+        __syncthreads();   // tensor memory and operand tiles are rewritten by the next tile
+    }
+    if (s.abort) {
+        tc::mbar_wait(&s.mbar, phase, 20000000LL);
+        if (tid == 0) atomicOr(err, kErrTimeout);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc<TM_COLS>(s.taddr);
+}
+
 template <class S, int N, class K>
 int launch_tc(K kernel, const EdgeArgs& a, int rpg, int num_sms, cudaStream_t st) {
     const int64_t groups = (a.n + rpg - 1) / rpg;
@@ -1602,6 +1925,32 @@ int launch_edge_fwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int
     if (!(m.d.F == TF && m.d.lmax == TLMAX) || !a.w->W3sw || !a.err || !a.sched || !a.geo)
         return MP_ERR_UNSUPPORTED;
     if (a.n == 0) return MP_OK;
+    if (a.first && a.vfirst && a.species && a.emb && a.n_species >= 1 && a.n_species <= SMAX0) {
+        // layer 0 by hidden unit: G per row (scratch a.vfirst), then A from G
+        int rc = MP_OK;
+        switch (a.n_species) {
+            case 1: rc = launch_tc<SmemF0<1>, F0Cfg<1>::NWG>(k_edge_fwd0_tc<1>, a, RPG_F, num_sms, st); break;
+            case 2: rc = launch_tc<SmemF0<2>, F0Cfg<2>::NWG>(k_edge_fwd0_tc<2>, a, RPG_F, num_sms, st); break;
+            default: rc = launch_tc<SmemF0<3>, F0Cfg<3>::NWG>(k_edge_fwd0_tc<3>, a, RPG_F, num_sms, st); break;
+        }
+        if (rc != MP_OK) return rc;
+        const int64_t tiles = (a.n + AF_NT - 1) / AF_NT;
+        const int grid = (int)(tiles < num_sms ? tiles : num_sms);
+        auto run = [&](auto kernel, size_t smem) -> int {
+            MP_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+            kernel<<<grid, AF_NTH, smem, st>>>(a.n, a.vfirst, a.emb, a.w->W3sw, a.k.inv_navg,
+                                               a.Aout, tiles, a.err);
+            note_launch();
+            MP_CUDA_TRY(cudaGetLastError());
+            return MP_OK;
+        };
+        switch (a.n_species) {
+            case 1: return run(k_a_first_tc<1>, sizeof(AfSmem<1>) + 1024);
+            case 2: return run(k_a_first_tc<2>, sizeof(AfSmem<2>) + 1024);
+            default: return run(k_a_first_tc<3>, sizeof(AfSmem<3>) + 1024);
+        }
+    }
     return a.first
                ? launch_tc<SmemF<true>, FwdCfg<true>::NWG>(k_edge_fwd_tc<true>, a, RPG_F, num_sms, st)
                : launch_tc<SmemF<false>, FwdCfg<false>::NWG>(k_edge_fwd_tc<false>, a, RPG_F,
