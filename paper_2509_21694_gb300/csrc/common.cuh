@@ -138,7 +138,7 @@ struct Workspace {
         err, tmp, xw, perm_pos, pscr, pstats, red, headbuf, adam, sched, vir,
         corder,   // partition placement: cells in Morton order [ncell], sizes, offsets
         geo,      // tensor-core edge kernels: per edge (u_x, u_y, u_z, r) of a sub-system
-        vfirst;   // BF16 layer-0 adjoint: per atom, species and (l, m) the hidden-unit vectors V
+        vfirst;   // BF16 layer 0 by hidden unit: per atom, species and (l, m), G (forward) or V (adjoint)
     void release_all() {
         DevBuf* all[] = {&xl, &sp, &H, &A, &S, &G0, &G1, &alpha, &floc, &eatom, &esum, &fsum,
                          &ebuf, &err, &tmp, &xw, &perm_pos, &pscr, &pstats, &red, &headbuf,

@@ -293,7 +293,7 @@ struct EvalBufs {
     double* vtot;     // [9] all sub-systems', in sub-system order
     float4* geo;      // BF16: per edge (u, r) of the current sub-system
     float4* split;    // BF16: the sub-system's positions as FP32 pairs (2 n)
-    float* vfirst;    // BF16 layer-0 adjoint: hidden-unit vectors [n][S][NLM][kH], or null
+    float* vfirst;    // BF16 layer 0 by hidden unit: G or V [n][S][NLM][kH], or null
 };
 
 // Rows a pass must cover: atoms within `hops` hops of a root (a prefix of

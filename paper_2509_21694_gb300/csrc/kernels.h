@@ -36,9 +36,10 @@ struct EdgeArgs {
     // ends are both >= n_recv has zero adjoint on both sides and may be
     // skipped (<= 0: every row is a receiver)
     int64_t n_recv;
-    // BF16 layer-0 adjoint (tensor-core path): local species of every row, the
-    // embedding table [S][F], and scratch for the per-atom hidden-unit
-    // vectors V [n][S][NLM][H] (null: the channel-wise kernel is used)
+    // BF16 layer 0 by hidden unit (tensor-core path): local species of every
+    // row, the embedding table [S][F], and scratch [n][S][NLM][H] for the
+    // forward's per-row sums G and the adjoint's per-atom vectors V (null:
+    // the channel-wise kernels are used)
     const int32_t* species;
     const float* emb;
     int n_species;
