@@ -52,6 +52,8 @@
 // One thread issues the MMAs; completion is signalled through an mbarrier
 // whose waits are bounded (clock64): on a timeout the warpgroup sets an
 // error bit, stops, and the CTA frees its tensor memory and returns.
+#include <type_traits>
+
 #include "kernels.h"
 #include "tc.cuh"
 
@@ -1623,44 +1625,56 @@ __global__ void __launch_bounds__((F0Cfg<S>::NTH), 1)
             }
             tc::fence_before_sync();
             wg_sync(g);   // the a2 rows are complete (read below by hidden unit)
-#pragma unroll 2
-            for (int e = 0; e < SCF; ++e) {
-                const int lr = w.row[e];
-                if (lr < 0) break;
-                if (lr != cur) {
-                    if (cur >= 0) {
-                        write_row(cur, false);
-                        next = cur + 1;
+            // the chunk's edges in order, eight per step so that each edge's
+            // swizzled a2 column offset is a constant XOR pattern; the two
+            // halves of the warpgroup (warp-uniform) run their own loop, with
+            // their (l, m) rows fixed at compile time
+            auto run = [&](auto half) {
+                constexpr int HALF = decltype(half)::value;
+                const int c8 = hu >> 3, lo2 = (hu & 7) * 2;
+                bool done = false;
+#pragma unroll 1
+                for (int e8 = 0; e8 < SCF && !done; e8 += 8) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int e = e8 + k;
+                        const int lr = w.row[e];
+                        if (lr < 0) { done = true; break; }
+                        if (lr != cur) {
+                            if (cur >= 0) {
+                                write_row(cur, false);
+                                next = cur + 1;
+                            }
+                            for (int q = next; q < lr; ++q) write_row(q, true);
+                            next = lr;
+                            cur = lr;
+#pragma unroll
+                            for (int q = 0; q < S; ++q)
+#pragma unroll
+                                for (int i = 0; i < NL; ++i) acc[q][i] = 0.f;
+                        }
+                        const float a2 = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
+                            Bb + e * 128 + (((c8 ^ k) & 7) << 4) + lo2));
+                        const float4 yv = *reinterpret_cast<const float4*>(&w.Y[e][HALF ? 4 : 0]);
+                        // this half's (l, m) rows: Y_0 = 1, Y_1..Y_4 or Y_5..Y_8
+                        const float y[NL] = {HALF ? yv.x : 1.f, HALF ? yv.y : yv.x,
+                                             HALF ? yv.z : yv.y, HALF ? yv.w : yv.z,
+                                             HALF ? 0.f : yv.w};
+                        const int sp = S > 1 ? w.sj[e] : 0;
+#pragma unroll
+                        for (int q = 0; q < S; ++q) {
+                            if (S == 1 || q == sp) {
+#pragma unroll
+                                for (int i = 0; i < NL - HALF; ++i) acc[q][i] = fmaf(a2, y[i], acc[q][i]);
+                            }
+                        }
                     }
-                    for (int q = next; q < lr; ++q) write_row(q, true);
-                    next = lr;
-                    cur = lr;
-#pragma unroll
-                    for (int q = 0; q < S; ++q)
-#pragma unroll
-                        for (int i = 0; i < NL; ++i) acc[q][i] = 0.f;
                 }
-                const float a2 = __bfloat162float(
-                    *reinterpret_cast<const __nv_bfloat16*>(Bb + tc::sw128_off(e, hu)));
-                // this thread's (l, m) rows: Y_0 = 1, Y_1..Y_4 or Y_5..Y_8
-                float y[NL];
-                {
-                    const float4 yv = *reinterpret_cast<const float4*>(&w.Y[e][grp ? 4 : 0]);
-                    if (grp) {
-                        y[0] = yv.x; y[1] = yv.y; y[2] = yv.z; y[3] = yv.w; y[4] = 0.f;
-                    } else {
-                        y[0] = 1.f; y[1] = yv.x; y[2] = yv.y; y[3] = yv.z; y[4] = yv.w;
-                    }
-                }
-                const int sp = S > 1 ? w.sj[e] : 0;
-#pragma unroll
-                for (int q = 0; q < S; ++q) {
-                    if (S == 1 || q == sp) {
-#pragma unroll
-                        for (int i = 0; i < NL; ++i) acc[q][i] = fmaf(a2, y[i], acc[q][i]);
-                    }
-                }
-            }
+            };
+            if (grp)
+                run(std::integral_constant<int, 1>{});
+            else
+                run(std::integral_constant<int, 0>{});
             wg_sync(g);   // the tile and edge records are rewritten by the next chunk
         }
         if (!alive) break;

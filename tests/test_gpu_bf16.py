@@ -70,6 +70,22 @@ def test_bf16_depths_with_pair_term(mp, K):
     _check_bf16(_run(mp, d, w, s, K, mp.MP_BF16), _oracle(d, w, s, K), len(s.pos))
 
 
+def test_bf16_four_species(mp):
+    """Four species: the hidden-unit layer-0 forward handles up to three, so
+    this case runs the channel-wise layer-0 forward beside the hidden-unit
+    layer-0 adjoint (whose per-atom vectors V are formed for each of the
+    four species)."""
+    pos, box = synth.fcc((5, 5, 5), 3.6)
+    pos = synth.displace(pos, 0.1, 21)
+    sp = synth.assign_species(len(pos), (0.4, 0.3, 0.2, 0.1), 21)
+    assert set(np.unique(sp)) == {0, 1, 2, 3}
+    s = synth.System(pos, box, sp, np.ones(len(pos)), "alloy4")
+    d = synth.model_alloy(n_layers_full=2)
+    d.n_species = 4
+    w = synth.make_weights(d, 5)
+    _check_bf16(_run(mp, d, w, s, 2, mp.MP_BF16), _oracle(d, w, s, 2), len(s.pos))
+
+
 def test_bf16_close_to_fp32(mp):
     s = synth.alloy_fcc(cells=(6, 6, 6), seed=7)
     d = synth.model_alloy(n_layers_full=2)
