@@ -1375,7 +1375,10 @@ __global__ void __launch_bounds__((Bwd0Cfg<STRESS>::NTH), 1)
 #pragma unroll
                     for (int q = 0; q < TNLM; ++q) vjc[q] = __ldg(p + q * kH);
                 }
-                auto edge_step = [&](int e, float (&vj)[TNLM], float (&vjnext)[TNLM]) -> bool {
+                // k = e mod 4 (a literal at each call): rows 2 e and 2 e + 1 of
+                // the swizzled tile then have constant XOR patterns 2 k, 2 k + 1
+                const int c8 = hu >> 3, lo2 = (hu & 7) * 2;
+                auto edge_step = [&](int e, int k, float (&vj)[TNLM], float (&vjnext)[TNLM]) -> bool {
                     const int lr = w.row[e];
                     if (lr < 0) return false;
                     if (e + 1 < e0 + 32) {
@@ -1405,10 +1408,11 @@ __global__ void __launch_bounds__((Bwd0Cfg<STRESS>::NTH), 1)
 #pragma unroll
                         for (int q = 0; q < TNLM; ++q) vk[q] = __ldg(p + q * kH);
                     }
-                    const float a2 = __bfloat162float(
-                        *reinterpret_cast<const __nv_bfloat16*>(Bb + tc::sw128_off(2 * e, hu)));
-                    const float da2 = __bfloat162float(
-                        *reinterpret_cast<const __nv_bfloat16*>(Bb + tc::sw128_off(2 * e + 1, hu)));
+                    const unsigned char* brow = Bb + e * 256 + lo2;
+                    const float a2 = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
+                        brow + (((c8 ^ (2 * k)) & 7) << 4)));
+                    const float da2 = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
+                        brow + 128 + (((c8 ^ (2 * k + 1)) & 7) << 4)));
                     float Y[TNLM];
                     {
                         const float4 y0 = *reinterpret_cast<const float4*>(&w.Y[e][0]);
@@ -1459,9 +1463,11 @@ __global__ void __launch_bounds__((Bwd0Cfg<STRESS>::NTH), 1)
                     return true;
                 };
 #pragma unroll 1
-                for (int i = 0; i < 32; i += 2) {
-                    if (!edge_step(e0 + i, vjc, vjn)) break;
-                    if (!edge_step(e0 + i + 1, vjn, vjc)) break;
+                for (int i = 0; i < 32; i += 4) {
+                    if (!edge_step(e0 + i, 0, vjc, vjn)) break;
+                    if (!edge_step(e0 + i + 1, 1, vjn, vjc)) break;
+                    if (!edge_step(e0 + i + 2, 2, vjc, vjn)) break;
+                    if (!edge_step(e0 + i + 3, 3, vjn, vjc)) break;
                 }
                 wg_sync(g);   // the B tile and edge records are rewritten by the next chunk
             }
