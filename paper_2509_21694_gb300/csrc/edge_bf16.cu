@@ -1694,15 +1694,21 @@ __global__ void __launch_bounds__((F0Cfg<S>::NTH), 1)
     tc_teardown(s, phase, err, tid);
 }
 
-// A of 16 atoms per tile: D[128 x 16] = W3_q(l) . (G_s[lm] in three BF16
-// parts)^T for every (l, m) and species, then A[atom][lm][c] =
-// N_avg^-1 sum_s Emb[s][c] D_s[lm][c][atom].
-constexpr int AF_NT = 16;         // atoms per tile (MMA N)
+// A of 16 atoms per tile.  G_s (per species, (l, m) and hidden unit) is
+// split into three BF16 parts; the operand rows of one species are ordered
+// ((l, m), part, atom), so each radial path's rows are contiguous and one MMA
+// chain per path (N = 3 x 16 x the path's (l, m) count: 48, 144, 240)
+// computes W3_q . G^T for all of them.  The epilogue sums the three parts'
+// columns, weights them by Emb[s][c] and sums the species:
+//   A[atom][lm][c] = N_avg^-1 sum_s Emb[s][c] sum_part D_s[lm][part][c][atom].
+// The next tile's G is loaded into registers while the MMAs run.
+constexpr int AF_NT = 16;         // atoms per tile
 constexpr int AF_NTH = 512;       // threads: 16 atoms x 32 in the load phase
+constexpr int AF_COLS = TNLM * 3 * AF_NT;   // tensor-memory columns of one species (432)
 template <int S>
 struct alignas(1024) AfSmem {
     __nv_bfloat16 W3[3][128 * 64];              // paths R0, R1a, R2a (swizzled images)
-    __nv_bfloat16 X[TNLM][S][3][AF_NT * 64];    // G parts: (l, m), species, part
+    __nv_bfloat16 X[S][TNLM][3][AF_NT * 64];    // G parts: species, (l, m), part
     uint64_t mbar;
     uint32_t taddr;
     int abort;
@@ -1710,18 +1716,18 @@ struct alignas(1024) AfSmem {
 template <int S>
 constexpr bool af_fits() { return sizeof(AfSmem<S>) + 1024 <= 232448; }
 static_assert(af_fits<1>() && af_fits<SMAX0>(), "shared memory of k_a_first_tc");
-static_assert(TNLM * SMAX0 * AF_NT <= TM_COLS, "tensor memory of k_a_first_tc");
+static_assert(AF_COLS <= TM_COLS, "tensor memory of k_a_first_tc");
 
-// D[tmem, 128 x N] (+)= A(128 x 64 tile) . B(N x 64 tile)^T, four K = 16 steps.
+// D[tmem, 128 x N] = A(128 x 64 tile) . B(N x 64, N consecutive tile rows)^T,
+// four K = 16 steps.
 template <int N>
-__device__ __forceinline__ void mma_k64_acc(uint32_t d, const __nv_bfloat16* A,
-                                            const __nv_bfloat16* B, bool acc) {
+__device__ __forceinline__ void mma_k64_n(uint32_t d, const __nv_bfloat16* A,
+                                          const __nv_bfloat16* B) {
     const uint64_t ad = tc::desc_sw128(tc::smem_u32(A));
     const uint64_t bd = tc::desc_sw128(tc::smem_u32(B));
     constexpr uint32_t idesc = tc::idesc_bf16(128, N);
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk)
-        tc::mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc, (acc || kk > 0) ? 1u : 0u);
+    for (int kk = 0; kk < 4; ++kk) tc::mma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc, kk > 0 ? 1u : 0u);
 }
 
 template <int S>
@@ -1735,6 +1741,7 @@ __global__ void __launch_bounds__(AF_NTH, 1)
     const int ia = tid >> 5, q = tid & 31;            // load phase: atom, float4 slot
     const int lq = warp & 3, ag = warp >> 2;          // epilogue: lane quarter, atom group
     const int c = 32 * lq + lane;
+    constexpr int NV = (S * TNLM * 16 + 31) / 32;     // float4 slots of G per thread
     for (int p = 0; p < 3; ++p) {
         const int blk = p == 0 ? 0 : 2 * p - 1;
         const uint4* src = reinterpret_cast<const uint4*>(W3sw + (size_t)blk * 128 * 64);
@@ -1753,17 +1760,30 @@ __global__ void __launch_bounds__(AF_NTH, 1)
     float es[S];
 #pragma unroll
     for (int k = 0; k < S; ++k) es[k] = __ldg(&emb[k * 128 + c]);
-    uint32_t phase = 0;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    float4 gv[NV];
+    auto load = [&](int64_t tile) {   // this thread's slots r = q + 32 v of atom ia
         const int64_t atom = tile * AF_NT + ia;
-        // G of atom ia in three BF16 parts (each the rounding of what the
-        // previous parts leave), into the swizzled K-major operand tiles
-        for (int r = q; r < S * TNLM * 16; r += 32) {
+        const bool ok = tile < n_tiles && atom < n;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const int r = q + 32 * v;
+            gv[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ok && r < S * TNLM * 16)
+                gv[v] = __ldg(reinterpret_cast<const float4*>(G + (atom * S * TNLM) * kH) + r);
+        }
+    };
+    uint32_t phase = 0;
+    int64_t tile = blockIdx.x;
+    load(tile);
+    for (; tile < n_tiles; tile += gridDim.x) {
+        // this tile's G (in registers) in three BF16 parts, each the rounding
+        // of what the previous parts leave, into the swizzled operand rows
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const int r = q + 32 * v;
+            if (r >= S * TNLM * 16) break;
             const int sp = r / (TNLM * 16), lm = (r / 16) % TNLM, h4 = r & 15;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (atom < n)
-                v = __ldg(reinterpret_cast<const float4*>(G + ((atom * S + sp) * TNLM + lm) * kH) + h4);
-            float rr[4] = {v.x, v.y, v.z, v.w};
+            float rr[4] = {gv[v].x, gv[v].y, gv[v].z, gv[v].w};
             const uint32_t off = ia * 128 + ((((h4 >> 1) ^ (ia & 7)) & 7) << 4) + ((h4 & 1) << 3);
 #pragma unroll
             for (int part = 0; part < 3; ++part) {
@@ -1776,52 +1796,54 @@ __global__ void __launch_bounds__(AF_NTH, 1)
                 uint2 u;
                 u.x = *reinterpret_cast<const uint32_t*>(&lo);
                 u.y = *reinterpret_cast<const uint32_t*>(&hi);
-                *reinterpret_cast<uint2*>(reinterpret_cast<unsigned char*>(s.X[lm][sp][part]) + off) = u;
+                *reinterpret_cast<uint2*>(reinterpret_cast<unsigned char*>(s.X[sp][lm][part]) + off) = u;
             }
         }
         tc::fence_proxy_async();
         tc::fence_before_sync();
         __syncthreads();
-        if (tid == 0) {
-            tc::fence_after_sync();
-#pragma unroll 1
-            for (int lm = 0; lm < TNLM; ++lm) {
-                const int path = lm == 0 ? 0 : (lm < 4 ? 1 : 2);
-                for (int sp = 0; sp < S; ++sp) {
-                    const uint32_t d = s.taddr + AF_NT * (lm * S + sp);
+        float o[TNLM][4];
 #pragma unroll
-                    for (int part = 0; part < 3; ++part)
-                        mma_k64_acc<AF_NT>(d, s.W3[path], s.X[lm][sp][part], part > 0);
-                }
+        for (int lm = 0; lm < TNLM; ++lm)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) o[lm][r] = 0.f;
+        for (int sp = 0; sp < S; ++sp) {
+            if (tid == 0) {   // one chain per radial path: rows ((l, m), part, atom)
+                tc::fence_after_sync();
+                mma_k64_n<3 * AF_NT * 1>(s.taddr, s.W3[0], s.X[sp][0][0]);
+                mma_k64_n<3 * AF_NT * 3>(s.taddr + 3 * AF_NT * 1, s.W3[1], s.X[sp][1][0]);
+                mma_k64_n<3 * AF_NT * 5>(s.taddr + 3 * AF_NT * 4, s.W3[2], s.X[sp][4][0]);
+                tc::mma_commit(&s.mbar);
             }
-            tc::mma_commit(&s.mbar);
-        }
-        if (tc::mbar_wait(&s.mbar, phase))
-            phase ^= 1u;
-        else
-            s.abort = 1;
-        __syncthreads();
-        tc::fence_after_sync();
-        if (s.abort) break;
-        const int64_t i0 = tile * AF_NT + 4 * ag;
-        const uint32_t tcol = s.taddr + ((uint32_t)(32 * lq) << 16) + 4 * ag;
-#pragma unroll 1
-        for (int lm = 0; lm < TNLM; ++lm) {
-            float o[4] = {0.f, 0.f, 0.f, 0.f};
+            if (sp == 0) load(tile + gridDim.x);   // the next tile's G, meanwhile
+            if (tc::mbar_wait(&s.mbar, phase))
+                phase ^= 1u;
+            else
+                s.abort = 1;
+            __syncthreads();
+            tc::fence_after_sync();
+            if (s.abort) break;
+            const uint32_t tcol = s.taddr + ((uint32_t)(32 * lq) << 16) + 4 * ag;
 #pragma unroll
-            for (int sp = 0; sp < S; ++sp) {
-                float dv[4];
-                tc::tmem_ld4(tcol + AF_NT * (lm * S + sp), dv);
+            for (int lm = 0; lm < TNLM; ++lm) {
+                float d0[4], d1[4], d2[4];
+                tc::tmem_ld4(tcol + AF_NT * (3 * lm + 0), d0);
+                tc::tmem_ld4(tcol + AF_NT * (3 * lm + 1), d1);
+                tc::tmem_ld4(tcol + AF_NT * (3 * lm + 2), d2);
                 tc::tmem_wait_ld();
 #pragma unroll
-                for (int r = 0; r < 4; ++r) o[r] = fmaf(es[sp], dv[r], o[r]);
+                for (int r = 0; r < 4; ++r) o[lm][r] = fmaf(es[sp], d0[r] + d1[r] + d2[r], o[lm][r]);
             }
+            tc::fence_before_sync();
+            __syncthreads();   // tensor memory is rewritten by the next species or tile
+        }
+        if (s.abort) break;
+        const int64_t i0 = tile * AF_NT + 4 * ag;
+#pragma unroll
+        for (int lm = 0; lm < TNLM; ++lm)
 #pragma unroll
             for (int r = 0; r < 4; ++r)
-                if (i0 + r < n) Aout[((i0 + r) * TNLM + lm) * 128 + c] = o[r] * inv_navg;
-        }
-        tc::fence_before_sync();
-        __syncthreads();   // tensor memory and operand tiles are rewritten by the next tile
+                if (i0 + r < n) Aout[((i0 + r) * TNLM + lm) * 128 + c] = o[lm][r] * inv_navg;
     }
     if (s.abort) {
         tc::mbar_wait(&s.mbar, phase, 20000000LL);
