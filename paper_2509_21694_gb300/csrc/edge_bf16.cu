@@ -4,10 +4,10 @@
 // Shapes compiled: F = 128, lmax = 2, H = 64.
 //
 // A CTA holds one copy of the W1 / W2 / W3 operand tiles and runs
-// independent warpgroups (six or five in the forward, six or four in the
-// adjoint, whose per-thread state needs more registers); each warpgroup owns
-// a stream of receiver-row groups, its tensor-memory columns (80 / 96
-// forward, 64 / 128 adjoint), an mbarrier and a named barrier, so one
+// independent warpgroups (six or five in the forward, four in the
+// later-layer adjoint, whose per-thread state needs more registers); each
+// warpgroup owns a stream of receiver-row groups, its tensor-memory columns
+// (80 / 96 forward, 128 adjoint), an mbarrier and a named barrier, so one
 // warpgroup's MMAs overlap the others' CUDA-core work.  The geometry (unit
 // vector and r of every edge) is formed once per sub-system by
 // k_edge_geometry and read here.
@@ -44,11 +44,12 @@
 // (later-layer forward) or one (adjoint) edges at a time.
 // The MLP's hidden activations use the hardware tanh for the sigmoid: they
 // are rounded to BF16 for the next contraction anyway.
-// The adjoint of layer 0 runs by hidden unit instead (k_v_first and
-// k_edge_bwd0_tc, below): there the senders' features are species
-// embeddings, so its channel sums factor through the last radial layer and
-// are formed once per atom; the channel-wise layer-0 adjoint remains for a
-// caller that provides no scratch for those per-atom vectors.
+// Layer 0 runs by hidden unit instead (k_v_first and k_edge_bwd0_tc for the
+// adjoint, k_edge_fwd0_tc and k_a_first_tc for the forward, below): there
+// the senders' features are species embeddings, so its channel sums factor
+// through the last radial layer.  The channel-wise forward above still
+// serves layer 0 for more than three species; the channel-wise adjoint
+// serves the later layers only.
 // One thread issues the MMAs; completion is signalled through an mbarrier
 // whose waits are bounded (clock64): on a timeout the warpgroup sets an
 // error bit, stops, and the CTA frees its tensor memory and returns.
@@ -62,10 +63,6 @@ namespace mp {
 namespace {
 
 constexpr int TF = 128, TLMAX = 2, TNLM = 9;
-// Adjoint: four warpgroups of 128 threads at up to 128 registers each.
-constexpr int NWG = 4;             // warpgroups per CTA
-constexpr int NTH = 128 * NWG;     // threads per CTA
-constexpr int WG_COLS = 128;       // tensor-memory columns per warpgroup (D1 and D2 share them)
 // Forward: its per-thread state is smaller, so more warpgroups hide more of
 // the gathers' latency: six for layer 0 (one gathered value per edge), five
 // for the later layers (96 registers, which also hold a ring of the next
@@ -150,22 +147,13 @@ struct alignas(1024) WgStateF {
     int abort;
 };
 
-// Adjoint: four warpgroups at up to 128 registers, except layer 0 without
-// the stress (no sender gradients, one gathered h value per edge), which
-// runs six at 80 registers: its compensated force sums live in shared
-// memory, seven of the nine sender alpha components are requested one edge
-// ahead and the other two when their edge starts, and its three radial
-// paths need 64 tensor-memory columns.
-template <bool FIRST, bool STRESS>
+// Adjoint of the later layers (channel-wise): four warpgroups at up to 128
+// registers, 128 tensor-memory columns each.
+template <bool STRESS>
 struct BwdCfg {
-    static constexpr int NWG = (FIRST && !STRESS) ? 6 : 4;
+    static constexpr int NWG = 4;
     static constexpr int NTH = 128 * NWG;
-    static constexpr int COLS = (FIRST && !STRESS) ? 64 : 128;
-    // the compensated row force sums in shared memory instead of registers
-    static constexpr bool FKS = FIRST && !STRESS;
-    // sender alpha components requested one edge ahead (the rest are
-    // requested when their edge starts)
-    static constexpr int PFN = FKS ? 7 : 9;
+    static constexpr int COLS = 128;
 };
 
 template <int NP, class WG, int N>
@@ -174,20 +162,18 @@ struct SmemT {
     WG wg[N];
     uint32_t taddr;
 };
-template <bool FIRST, bool STRESS>
-using SmemB = SmemT<FIRST ? 3 : 5, WgState<STRESS, BwdCfg<FIRST, STRESS>::FKS>,
-                    BwdCfg<FIRST, STRESS>::NWG>;   // adjoint
+template <bool STRESS>
+using SmemB = SmemT<5, WgState<STRESS, false>, BwdCfg<STRESS>::NWG>;   // adjoint, later layers
 template <bool FIRST>
 using SmemF = SmemT<FIRST ? 3 : 5, WgStateF, FwdCfg<FIRST>::NWG>;          // forward
 template <class S>
 constexpr bool smem_fits() { return sizeof(S) + 1024 <= 232448; }
-static_assert(smem_fits<SmemB<true, false>>() && smem_fits<SmemB<false, false>>() &&
-              smem_fits<SmemB<true, true>>() && smem_fits<SmemB<false, true>>(),
+static_assert(smem_fits<SmemB<false>>() && smem_fits<SmemB<true>>(),
               "shared memory of the edge adjoint");
 static_assert(smem_fits<SmemF<true>>() && smem_fits<SmemF<false>>(),
               "shared memory of the edge forward");
-static_assert(BwdCfg<true, false>::NWG * BwdCfg<true, false>::COLS <= TM_COLS &&
-              NWG * WG_COLS <= TM_COLS && FwdCfg<true>::NWG * FwdCfg<true>::COLS <= TM_COLS &&
+static_assert(BwdCfg<false>::NWG * BwdCfg<false>::COLS <= TM_COLS &&
+              FwdCfg<true>::NWG * FwdCfg<true>::COLS <= TM_COLS &&
               FwdCfg<false>::NWG * FwdCfg<false>::COLS <= TM_COLS, "tensor memory");
 
 // The dynamic shared memory rounded up to a 1024-byte boundary (the swizzled
@@ -600,13 +586,13 @@ __device__ __forceinline__ void warp_sum_pair(float& hi, float& lo) {
 
 // Adjoint tile rows: row 2 e holds edge e, row 2 e + 1 its r-tangent, so a
 // 16-row slice is 8 edges and D2 columns (2 i, 2 i + 1) are (R, dR/dr).
-template <bool FIRST, bool STRESS>
-__global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
+template <bool STRESS>
+__global__ void __launch_bounds__((BwdCfg<STRESS>::NTH), 1)
     k_edge_bwd_tc(EdgeArgs a, LayerW wl, int64_t n_groups, int* err) {
-    using PP = TPaths<FIRST>;
-    using Cfg = BwdCfg<FIRST, STRESS>;
+    using PP = TPaths<false>;
+    using Cfg = BwdCfg<STRESS>;
     extern __shared__ unsigned char smem_raw[];
-    auto& s = smem_as<SmemB<FIRST, STRESS>>(smem_raw);
+    auto& s = smem_as<SmemB<STRESS>>(smem_raw);
     const int tid = threadIdx.x, g = tid >> 7, lt = tid & 127, warp = tid >> 5, lane = tid & 31;
     const int c = lt;
     auto& w = s.wg[g];
@@ -614,7 +600,7 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
     const float* __restrict__ Alpha = a.Alpha;
     const float* __restrict__ Gout = a.Gout;
     float* __restrict__ Gin = a.Gin;
-    tc_setup<Cfg::NTH>(s, wl, PP::NP, FIRST, tid);
+    tc_setup<Cfg::NTH>(s, wl, PP::NP, false, tid);
     const uint32_t tb = s.taddr + Cfg::COLS * g;
     const uint32_t tl = tb + ((uint32_t)(32 * (warp & 3)) << 16);
     uint32_t phase = 0;
@@ -635,11 +621,8 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
         // this channel's share of the row force: FP32 partial sums over a slice
         // (fs), folded into a compensated row sum (fk, fc) once per slice
         float fk_r[3] = {0.f, 0.f, 0.f}, fc_r[3] = {0.f, 0.f, 0.f}, fs[3] = {0.f, 0.f, 0.f};
-        // (fk, fc) in registers, or in shared memory where registers bound the
-        // warpgroups per SM
-        float* __restrict__ fkc = &w.fkc[0][lt];
-        auto FK = [&](int q) -> float& { return Cfg::FKS ? fkc[q * 128] : fk_r[q]; };
-        auto FC = [&](int q) -> float& { return Cfg::FKS ? fkc[(3 + q) * 128] : fc_r[q]; };
+        auto FK = [&](int q) -> float& { return fk_r[q]; };
+        auto FC = [&](int q) -> float& { return fc_r[q]; };
         // with STRESS: this channel's share of the row's virial sum_e g_e (x) d_e
         // (a global sum, so plain FP32 per row suffices)
         float va[STRESS ? 9 : 1];
@@ -660,7 +643,7 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
         for (int q = 0; q < TNLM; ++q) gacc[q] = ak[q] = hk[q] = 0.f;
         int cur = -1, next = 0;
         auto flush = [&](int lr, bool with_acc) {
-            if (!FIRST) {
+            {
                 const int64_t base = ((r0 + lr) * TNLM) * TF + c;
 #pragma unroll
                 for (int q = 0; q < TNLM; ++q)
@@ -801,8 +784,8 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                         const int64_t jb = ((int64_t)w.col[sl * 8] * TNLM) * TF + c;
 #pragma unroll
                         for (int q = 0; q < TNLM; ++q) {
-                            if (q < Cfg::PFN) ajc[q] = __ldg(Alpha + jb + q * TF);
-                            hjc[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + jb + q * TF);
+                            ajc[q] = __ldg(Alpha + jb + q * TF);
+                            hjc[q] = __ldg(Hin + jb + q * TF);
                         }
                     }
                     if (!wg_wait(w, phase, g)) { alive = false; break; }
@@ -814,11 +797,6 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                         const int e = sl * 8 + i;
                         const int lr = w.row[e];
                         if (lr < 0) return false;
-                        if (Cfg::PFN < TNLM) {   // this edge's components not requested ahead
-                            const int64_t jc = ((int64_t)w.col[e] * TNLM) * TF + c;
-#pragma unroll
-                            for (int q = Cfg::PFN; q < TNLM; ++q) ajc[q] = __ldg(Alpha + jc + q * TF);
-                        }
                         float R[PP::NP], dR[PP::NP];
 #pragma unroll
                         for (int q = 0; q < PP::NP; ++q) {
@@ -831,8 +809,8 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                             const int64_t jn = ((int64_t)w.col[e + 1] * TNLM) * TF + c;
 #pragma unroll
                             for (int q = 0; q < TNLM; ++q) {
-                                if (q < Cfg::PFN) ajn[q] = __ldg(Alpha + jn + q * TF);
-                                hjn[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + jn + q * TF);
+                                ajn[q] = __ldg(Alpha + jn + q * TF);
+                                hjn[q] = __ldg(Hin + jn + q * TF);
                             }
                         }
                         if (lr != cur) {
@@ -849,7 +827,7 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                             for (int q = 0; q < TNLM; ++q) {
                                 gacc[q] = 0.f;
                                 ak[q] = __ldg(Alpha + base + q * TF);
-                                hk[q] = (FIRST && q > 0) ? 0.f : __ldg(Hin + base + q * TF);
+                                hk[q] = __ldg(Hin + base + q * TF);
                             }
 #pragma unroll
                             for (int q = 0; q < 3; ++q) FK(q) = FC(q) = 0.f;
@@ -870,29 +848,7 @@ __global__ void __launch_bounds__((BwdCfg<FIRST, STRESS>::NTH), 1)
                         const float hj0 = hjc[0], hk0 = hk[0];
                         float gr, gy[TNLM];
                         gy[0] = 0.f;
-                        if (FIRST) {
-                            // layer 0 (no l >= 1 inputs): P_lm = hj0 ak_lm -+ hk0 aj_lm enters
-                            // both the radial term (through P_l . Y_l) and dE/dY (R_la P_lm)
-                            // (gy carries the harmonics' factors sqrt3 / sqrt15, see
-                            // sph_grad_prescaled)
-                            const float r1 = kS3 * R[PP::sla(1)], r2 = kS15 * R[PP::sla(2)];
-                            float s1 = 0.f, s2 = 0.f;
-#pragma unroll
-                            for (int m = 0; m < 3; ++m) {
-                                const float P = fmaf(hj0, ak[1 + m], -hk0 * ajc[1 + m]);
-                                s1 = fmaf(P, Y[1 + m], s1);
-                                gy[1 + m] = r1 * P;
-                            }
-#pragma unroll
-                            for (int m = 0; m < 5; ++m) {
-                                const float P = fmaf(hj0, ak[4 + m], hk0 * ajc[4 + m]);
-                                s2 = fmaf(P, Y[4 + m], s2);
-                                gy[4 + m] = r2 * P;
-                            }
-                            gr = fmaf(ak[0], hj0, ajc[0] * hk0) * dR[0];
-                            gr = fmaf(s1, dR[PP::sla(1)], gr);
-                            gr = fmaf(s2, dR[PP::sla(2)], gr);
-                        } else {
+                        {
                             // Y-weighted sums of the sender's (j) and receiver's (k) alpha
                             float sj1 = 0.f, sk1 = 0.f, sj2 = 0.f, sk2 = 0.f;
 #pragma unroll
@@ -1544,7 +1500,7 @@ __global__ void __launch_bounds__((F0Cfg<S>::NTH), 1)
     using Cfg = F0Cfg<S>;
     extern __shared__ unsigned char smem_raw[];
     auto& s = smem_as<SmemF0<S>>(smem_raw);
-    const int tid = threadIdx.x, g = tid >> 7, lt = tid & 127, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, g = tid >> 7, lt = tid & 127, warp = tid >> 5;
     const int hu = lt & 63, grp = lt >> 6;
     const int lm0 = grp ? 5 : 0;
     constexpr int NL = 5;              // (l, m) rows per thread (4 used by the second half)
@@ -2026,15 +1982,12 @@ int launch_edge_bwd_bf16(const Model& m, const EdgeArgs& a, cudaStream_t st, int
                      : launch_tc<SmemB0<false>, Bwd0Cfg<false>::NWG>(k_edge_bwd0_tc<false>, a,
                                                                        RPG_B, num_sms, st);
     }
-    if (a.vir)
-        return a.first ? launch_tc<SmemB<true, true>, BwdCfg<true, true>::NWG>(
-                             k_edge_bwd_tc<true, true>, a, RPG_B, num_sms, st)
-                       : launch_tc<SmemB<false, true>, BwdCfg<false, true>::NWG>(
-                             k_edge_bwd_tc<false, true>, a, RPG_B, num_sms, st);
-    return a.first ? launch_tc<SmemB<true, false>, BwdCfg<true, false>::NWG>(
-                         k_edge_bwd_tc<true, false>, a, RPG_B, num_sms, st)
-                   : launch_tc<SmemB<false, false>, BwdCfg<false, false>::NWG>(
-                         k_edge_bwd_tc<false, false>, a, RPG_B, num_sms, st);
+    // layer 0 runs only by hidden unit (above), which needs the scratch
+    if (a.first) return MP_ERR_UNSUPPORTED;
+    return a.vir ? launch_tc<SmemB<true>, BwdCfg<true>::NWG>(k_edge_bwd_tc<true>, a, RPG_B,
+                                                             num_sms, st)
+                 : launch_tc<SmemB<false>, BwdCfg<false>::NWG>(k_edge_bwd_tc<false>, a, RPG_B,
+                                                               num_sms, st);
 }
 
 }  // namespace mp
