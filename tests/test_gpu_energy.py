@@ -104,6 +104,34 @@ def test_isolated_atoms_and_empty_rows(mp):
     _check(_gpu(mp, d, w, s, 2), _ref(d, w, s, 2), len(s.pos))
 
 
+def test_isolated_atoms_and_empty_rows_bf16(mp):
+    """The same sparse gas through the BF16 tensor-core path (two species):
+    rows without edges get zero per-row sums in the layer-0 forward by
+    hidden unit and no force share in the adjoint; BF16 gates."""
+    rng = np.random.default_rng(4)
+    box = np.array([40.0, 40.0, 40.0])
+    pos = [rng.uniform(0, 40, 3) for _ in range(30)]
+    pos += [np.array([20.0, 20.0, 20.0]) + rng.normal(0, 1.2, 3) for _ in range(12)]
+    pos = np.array(pos)
+    sp = (np.arange(len(pos)) % 2).astype(np.int32)
+    s = synth.System(pos, box, sp, np.full(len(pos), 63.5))
+    d = synth.model_alloy(n_layers_full=2)
+    d.rep_eps = 0.5
+    w = synth.make_weights(d, 3)
+    E, F, Ei = _gpu(mp, d, w, s, 2, precision=mp.MP_BF16)
+    Er, Eir, Fr = _ref(d, w, s, 2)
+    frms = np.sqrt((Fr ** 2).mean())
+    erms = np.sqrt((Eir ** 2).mean())
+    assert np.sqrt(((F - Fr) ** 2).mean()) <= 1e-2 * frms
+    assert abs(E - Er) <= 5e-3 * len(pos) * erms
+    # isolated atoms: no force, the readout energy of their embedding only
+    iso = [i for i in range(30) if np.all(np.linalg.norm(
+        (pos - pos[i] + box / 2) % box - box / 2, axis=1)[np.arange(len(pos)) != i] >= d.r_cut)]
+    assert iso
+    assert np.all(F[iso] == 0.0)
+    assert np.allclose(Ei[iso], Eir[iso], rtol=0, atol=1e-5 * erms)
+
+
 def test_autograd_function_matches(mp):
     s, d = synth.cu_fcc_small(), synth.model_c1()
     w = synth.make_weights(d, 0)
