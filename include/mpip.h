@@ -58,7 +58,11 @@ extern "C" {
 #define MP_FP32  0   /* every contraction in FP32 on CUDA cores               */
 #define MP_BF16  1   /* radial-MLP and node GEMM operands in BF16 on tcgen05
                         tensor cores, FP32 accumulation; geometry, messages,
-                        features and forces stay FP32                         */
+                        features and forces stay FP32.  At layer 0 (inputs =
+                        species embeddings) the last radial layer's product
+                        is applied to per-row or per-atom sums over hidden
+                        units instead of to every edge: the same sums in
+                        another order, with the BF16 weight values        */
 #define MP_HALO_GEOM 0   /* halo = atoms within K r_c (z) of the slab         */
 #define MP_HALO_BFS  1   /* halo = atoms within K edges of a root (Stage 2)   */
 
